@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark of the FTLE hot path: FTLE points/s for one pass of the whole path (RK4 flowmap,
+least-squares gradient / Cauchy-Green / lambda_max / FTLE, FP64 refinement of float-sensitive
+nodes) over a synthetic workload, inputs resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 1] [--impl ours|reference]
+
+Default workload: 2048 x 1024 jittered triangle mesh (2,097,152 nodes, 6-neighbour CSR) over
+[0,2] x [0,1], double gyre A=0.1 eps=0.25 omega=2pi/10, RK4 dt=0.01 over T=15 (1500 steps),
+compensated-float advection with the FP64 path for float-sensitive nodes.
+
+Each step's kernels are bracketed by CUDA events on the launching stream; L2 is flushed by a
+320 MiB write between steps, outside the events.  Prints one JSON line (rank 0).
+`--impl reference` times the FP64 CPU oracle on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "FTLE points/sec (flowmap+gradient+lambda_max) at stated tol"
+UNIT = "points/s"
+FLUSH_BYTES = 320 << 20
+
+
+# Algorithmic FP32 flops of one compensated RK4 step per node (FMA = 2 flops; one sincospi or
+# sincos counted as 20 flops: argument reduction plus degree-7/8 minimax polynomials).
+FLOPS_PER_POINT_STEP = {"dg": 402, "abc": 432}
+
+
+def peak_fp32_tflops(sms: int, mhz: float) -> float:
+    """FP32 FMA throughput: 128 lanes per SM, 2 flops per FMA."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def load_peaks() -> dict:
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return json.loads(p.read_text())
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.out = Path(os.environ.get("TMPDIR", "/tmp")) / f"ftle_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.fh = open(self.out, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in self.out.read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.bus_id and self.bus_id[-12:] not in parts[1].lower():
+                continue
+            rows.append(parts)
+        self.out.unlink(missing_ok=True)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+
+
+def oracle_window(w, rows_lo: int, rows_hi: int):
+    """Oracle FTLE of lattice rows [rows_lo, rows_hi) of a 2D workload (nodes plus a one-row halo)."""
+    import numpy as np
+
+    import oracle as O
+
+    nx = w.mesh.shape[0]
+    nodes = np.arange(rows_lo * nx, rows_hi * nx)
+    t0 = time.perf_counter()
+    out = O.ftle_sample(w.flow.kind, w.flow.params, w.mesh.coords, w.mesh.row_ptr, w.mesh.col_idx, nodes, w.T, w.dt)
+    return len(nodes), time.perf_counter() - t0, out
+
+
+def oracle_block(w, n_nodes: int, seed: int = 0):
+    """Oracle FTLE of a contiguous block of nodes of any workload (2D or 3D)."""
+    import numpy as np
+
+    import oracle as O
+
+    start = (seed * 7919 * 1024) % max(1, w.mesh.n_nodes - n_nodes)
+    nodes = np.arange(start, start + n_nodes)
+    t0 = time.perf_counter()
+    O.ftle_sample(w.flow.kind, w.flow.params, w.mesh.coords, w.mesh.row_ptr, w.mesh.col_idx, nodes, w.T, w.dt)
+    return len(nodes), time.perf_counter() - t0
+
+
+def cpu_sample_size(w, target_s: float) -> int:
+    """Nodes of the workload the oracle processes in about target_s seconds on this host."""
+    import oracle as O
+
+    probe = 2048 if w.mesh.dim == 2 else 1024
+    n, dt = oracle_block(w, probe)
+    rate = n / max(dt, 1e-3)
+    del O
+    return int(max(probe, min(w.mesh.n_nodes // 2, rate * target_s)))
+
+
+def run_reference(args, w, world, rank):
+    """FP64 CPU oracle as the reference arm: each step a bounded sample of the same workload."""
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.build()
+    n_per_step = cpu_sample_size(w, 4.0)
+    for k in range(args.warmup):
+        oracle_block(w, n_per_step, seed=k)
+    times = []
+    for k in range(args.steps):
+        n, dt = oracle_block(w, n_per_step, seed=args.warmup + k)
+        times.append(dt)
+    value = n_per_step * args.steps / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "nodes": w.mesh.n_nodes, "steps_rk4": w.n_steps, "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{n_per_step} contiguous nodes of {w.name} per step (full path: RK4 + QR "
+                                   f"least squares + Jacobi), one-row halo advected too"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", type=int, default=1, help="preset index (0..2; 1 is the benchmark workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world, rank, local = dist_setup()
+    from paper_2408_02758_gb300 import inputs as I
+
+    w = I.preset(args.workload)
+
+    if args.impl == "reference":
+        run_reference(args, w, world, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2408_02758_gb300 import ftle
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    ftle.lib()
+
+    # CPU baseline first (before any GPU work, so nothing forked or threaded interferes)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+
+        O.build()
+        n_cpu = cpu_sample_size(w, 12.0)
+        n_done, t_cpu = oracle_block(w, n_cpu, seed=1)
+        cpu = {"value": n_done / t_cpu, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"{n_done} contiguous nodes of {w.name} (full path, FP64 oracle as it stands), "
+                         f"{t_cpu:.1f} s"}
+
+    dm = ftle.DeviceMesh.from_mesh(w.mesh, device=dev)
+    prec = w.precision
+    n = w.mesh.n_nodes
+    phi = ftle.flowmap_empty(w.mesh.dim, n, prec, device=dev)
+    out = ftle.ftle_out_empty(n, prec, device=dev)
+    ws = ftle.workspace_empty(ftle.ftle_workspace_bytes(n), device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    K, W = args.steps, args.warmup
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(W + K)]
+
+    def step(k):
+        flush.fill_(float(k))
+        e = ev[k]
+        e[0].record(stream)
+        ftle.ftle_advect(dm, w.flow, 0.0, w.T, w.dt, prec, phi, stream=sh)
+        e[1].record(stream)
+        ftle.ftle_gradient_eig(dm, phi, prec, w.T, out, None, ws, stream=sh)
+        e[2].record(stream)
+        ftle.ftle_refine(dm, w.flow, 0.0, w.T, w.dt, prec, phi, out, None, ws, stream=sh)
+        e[3].record(stream)
+
+    with torch.cuda.stream(stream):
+        for k in range(W):
+            step(k)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        bus = None
+        try:
+            bus = torch.cuda.get_device_properties(dev).pci_bus_id
+        except Exception:
+            bus = None
+        clocks = ClockSampler(bus)
+        clocks.start()
+        time.sleep(0.3)
+        t_wall = time.perf_counter()
+        for k in range(W, W + K):
+            step(k)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop()
+    counters = ftle.ftle_read_counters(ws, stream=sh)
+
+    t_step = [ev[k][0].elapsed_time(ev[k][3]) for k in range(W, W + K)]
+    t_adv = [ev[k][0].elapsed_time(ev[k][1]) for k in range(W, W + K)]
+    t_grad = [ev[k][1].elapsed_time(ev[k][2]) for k in range(W, W + K)]
+    t_ref = [ev[k][2].elapsed_time(ev[k][3]) for k in range(W, W + K)]
+    ms = sum(t_step) / K
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * world / (ms / 1000.0)
+
+    # end to end through the host-buffer entry point (pinned buffers, copies inside the timing)
+    e2e = None
+    if args.e2e_steps > 0:
+        ch = torch.from_numpy(np.ascontiguousarray(w.mesh.coords)).pin_memory()
+        rp = torch.from_numpy(w.mesh.row_ptr).pin_memory()
+        ci = torch.from_numpy(w.mesh.col_idx).pin_memory()
+        oh = torch.empty(n, dtype=torch.float64 if prec == "fp64" else torch.float32).pin_memory()
+        hws = ftle.workspace_empty(ftle.ftle_host_workspace_bytes(w.mesh.dim, n, w.mesh.nnz, prec), device=dev)
+        for _ in range(2):
+            ftle.ftle_compute_host(ch, rp, ci, w.flow, 0.0, w.T, w.dt, prec, oh, hws, stream=sh)
+        te = []
+        for _ in range(args.e2e_steps):
+            flush.fill_(0.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ftle.ftle_compute_host(ch, rp, ci, w.flow, 0.0, w.T, w.dt, prec, oh, hws, stream=sh)
+            te.append(time.perf_counter() - t0)
+        h2d = ch.numel() * ch.element_size() + rp.numel() * 4 + ci.numel() * 4
+        e2e = {"value": n / statistics.mean(te), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(oh.numel() * oh.element_size())}
+        del hws
+
+    if rank != 0:
+        return
+    peaks = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    kind = "dg" if w.flow.kind == I.DOUBLE_GYRE else "abc"
+    adv_ms = statistics.mean(t_adv)
+    flops = n * w.n_steps * FLOPS_PER_POINT_STEP[kind]
+    achieved = flops / (adv_ms / 1000.0) / 1e12
+    peak = peak_fp32_tflops(sms, float(peaks.get("sm_max_mhz", 2070.0)))
+    nnz = w.mesh.nnz
+    phi_b = 8 * w.mesh.dim * n if prec in ("fp32c", "fp64") else 4 * w.mesh.dim * n
+    coord_b = w.mesh.coords.dtype.itemsize * w.mesh.dim * n
+    grad_bytes = 4 * (n + 1) + 4 * nnz + coord_b + phi_b + (8 if prec == "fp64" else 4) * n
+    grad_ms = statistics.mean(t_grad)
+    prof = ROOT / "profiles" / f"traffic_{w.name}.json"
+    traffic = json.loads(prof.read_text()) if prof.exists() else {}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "nodes": n, "nnz": nnz, "steps_rk4": w.n_steps, "T": w.T, "dt": w.dt,
+                   "precision": prec, "l2": "flushed between steps (320 MiB write, outside the events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "k_advect (RK4 flowmap)", "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                                    "(max SM clock of measured peaks)",
+                     "flops_per_point_step": FLOPS_PER_POINT_STEP[kind], "ms": adv_ms,
+                     "traffic": traffic.get("k_advect")},
+        "roofline_gradient": {"kernel": "gradient stage (k_grad_f32 + FP64 fix-up + counter memset)", "bound": "hbm",
+                              "achieved": grad_bytes / (grad_ms / 1000.0) / 1e9, "peak": peaks.get("hbm_gbs"),
+                              "unit": "GB/s", "frac": grad_bytes / (grad_ms / 1000.0) / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                              "bytes_per_launch": grad_bytes, "ms": grad_ms, "traffic": traffic.get("k_grad_f32")},
+        "stage_ms": {"advect": adv_ms, "gradient": grad_ms, "refine": statistics.mean(t_ref),
+                     "wall_per_step_incl_flush": 1000 * t_wall / K},
+        "counters": counters,
+        "clocks": clk,
+        "gpu_launches": 6 * K,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * ftle.h - C-ABI of libftle.so, the GB300 (sm_103a) FTLE hot path.
+ *
+ * What is computed (arXiv 2408.02758, "Finite-Time Lyapunov Exponent Calculation on FPGA using
+ * High-Level Synthesis Tools"):
+ *   - the flowmap phi_T(x0) of every mesh node, the input of the paper's FTLE kernel
+ *     (Section 2.2: the flowmap and neighbour lists arrive precomputed), here integrated on the
+ *     GPU by classic RK4 through an analytic velocity field;
+ *   - the per-node FTLE core (Section 2.1, Table 1): least-squares flowmap gradient over the
+ *     node's precomputed neighbour list (Section 2.2, "decoupled" algorithm),
+ *     F = (sum_j dphi_j dx_j^T)(sum_j dx_j dx_j^T)^-1, dx_j = x_j - x_i, dphi_j = phi_j - phi_i,
+ *     the Cauchy-Green tensor C = F^T F, its largest eigenvalue lambda_max, and
+ *     FTLE = ln(sqrt(lambda_max)) / |T|.
+ * The paper's neighbour list is a fixed-width list padded with -1 (Section 2.2); this library
+ * takes the equivalent compressed form (CSR), where a short row simply has fewer entries.
+ *
+ * Conventions for every entry point:
+ *   - All array arguments are DEVICE pointers owned by the caller unless stated otherwise; the
+ *     library never frees or retains them past the call.  Nothing persistent is allocated on
+ *     the device (the batched plan holds a CUDA graph, see ftle_batch_plan_create).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue work and
+ *     return after launch; results are ready when the stream reaches that point.
+ *   - Return value: FTLE_OK (0) or a negative ftle_status.  Argument errors are detected on the
+ *     host before anything is launched.  Conditions found on the device (degenerate
+ *     neighbourhoods, nodes that took the FP64 path) are counted in the workspace header
+ *     (ftle_counters), never by a trap.  ftle_last_error() gives a message for the last failing
+ *     call of the calling thread.  No C++ exception crosses this boundary.
+ *   - Thread-safe for calls on distinct streams with distinct output/workspace buffers.
+ *   - Node coordinates are SoA: coords[d * n_nodes + i], d < dim.  Neighbour lists are CSR:
+ *     the neighbours of node i are col_idx[row_ptr[i] .. row_ptr[i+1]), int32, 0 <= j < n_nodes.
+ *   - T < 0 integrates backward in time; |T| enters the FTLE formula.  The RK4 step is
+ *     h = sign(T) |dt|, n = round(|T| / |dt|) steps from t0, stages at t_k, t_k + h/2 (twice),
+ *     t_k + h with t_k = t0 + k h.
+ */
+#ifndef FTLE_H
+#define FTLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FTLE_API_VERSION 1
+
+typedef enum ftle_status {
+  FTLE_OK = 0,
+  FTLE_EINVAL = -1,        /* bad argument: null pointer, size, mode or flow/dimension mismatch */
+  FTLE_ECUDA = -2,         /* a CUDA runtime call failed (message in ftle_last_error) */
+  FTLE_EWORKSPACE = -3,    /* workspace missing or smaller than the *_workspace_bytes query */
+  FTLE_EUNSUPPORTED = -4,  /* combination this build does not provide */
+  FTLE_ERANGE = -5         /* a size beyond a fixed limit (step count, nnz, static capacity) */
+} ftle_status;
+
+/* Velocity fields u(x, t); parameters in ftle_flow.p:
+ *   DOUBLE_GYRE (2D): p = {A, eps, omega}; f = a x^2 + b x, a = eps sin(omega t),
+ *                     b = 1 - 2 eps sin(omega t); u = -pi A sin(pi f) cos(pi y),
+ *                     v = pi A cos(pi f) sin(pi y) df/dx.
+ *   ABC (3D):         p = {A, B, C}; u = A sin z + C cos y, v = B sin x + A cos z,
+ *                     w = C sin y + B cos x.
+ *   LINEAR (2D/3D):   u = M x, M row-major dim x dim in p[0 .. dim*dim).
+ *   SADDLE (2D/3D):   u = (x, -y) in 2D, (x, -y, 0) in 3D. */
+typedef enum ftle_flow_kind {
+  FTLE_FLOW_DOUBLE_GYRE = 0,
+  FTLE_FLOW_ABC = 1,
+  FTLE_FLOW_LINEAR = 2,
+  FTLE_FLOW_SADDLE = 3
+} ftle_flow_kind;
+
+/* Arithmetic of the path.
+ *   FP64:  everything in double.  flowmap: double [dim][n]; ftle_out: double [n].
+ *   FP32:  plain float RK4 and float gradient.  flowmap: float [dim][n]; ftle_out: float [n].
+ *   FP32C: float RK4 stages with a compensated (two-sum) state and velocity evaluated at the
+ *          compensated stage point; the flowmap is stored as (hi, lo) float pairs,
+ *          flowmap: float2 [dim][n] (hi at even, lo at odd float index); gradient in float,
+ *          with the FP64 path for the nodes where float cancels (see ftle_options.refine_mu).
+ *          ftle_out: float [n]. */
+typedef enum ftle_precision { FTLE_PREC_FP64 = 0, FTLE_PREC_FP32 = 1, FTLE_PREC_FP32C = 2 } ftle_precision;
+
+typedef struct ftle_mesh {
+  int32_t dim;            /* 2 or 3 */
+  int32_t coord_fp64;     /* 0: coords are float, 1: coords are double */
+  int64_t n_nodes;        /* number of nodes, 0 <= n_nodes < 2^31 */
+  int64_t nnz;            /* entries of col_idx (= row_ptr[n_nodes]), < 2^31 */
+  const void* coords;     /* device, SoA [dim][n_nodes] */
+  const int32_t* row_ptr; /* device [n_nodes + 1], non-decreasing, row_ptr[0] = 0 */
+  const int32_t* col_idx; /* device [nnz] */
+} ftle_mesh;
+
+typedef struct ftle_flow {
+  int32_t kind;     /* ftle_flow_kind */
+  int32_t reserved; /* must be 0 */
+  double p[12];     /* parameters, layout per kind above */
+} ftle_flow;
+
+/* Device-side counters, at offset 0 of every workspace.  Read them with ftle_read_counters. */
+typedef struct ftle_counters {
+  unsigned long long n_flagged;    /* nodes whose gradient/eigenvalues went to the FP64 path */
+  unsigned long long n_degenerate; /* nodes with a rank-deficient neighbourhood: FTLE = NaN */
+  unsigned long long n_readvected; /* nodes re-advected in FP64 by ftle_refine */
+  unsigned long long reserved[5];
+} ftle_counters;
+
+/* Optional tuning; pass NULL for defaults.  Zero fields mean "default". */
+typedef struct ftle_options {
+  double refine_mu;       /* FP32/FP32C: nodes with lambda_max - 1 < refine_mu take the FP64
+                             path (default 0.1 when the field is 0; negative turns this test off,
+                             rank and conditioning checks still send nodes to FP64) */
+  int32_t advect_block;   /* threads per block of the advection kernel (multiple of 32) */
+  int32_t advect_blocks_per_sm; /* resident blocks per SM the advection grid is sized for */
+  int32_t grad_block;     /* threads per block of the gradient kernel (multiple of 32) */
+  int32_t grad_tile;      /* nodes per gradient tile (multiple of grad_block) */
+  int32_t reserved[4];
+} ftle_options;
+
+/* ---------------------------------------------------------------------------------- sizes */
+
+/* Bytes of a flowmap buffer for `precision` (0 on bad arguments). */
+size_t ftle_flowmap_bytes(int32_t dim, int64_t n_nodes, int32_t precision);
+
+/* Bytes of the workspace ftle_gradient_eig / ftle_refine / ftle_compute need for n_nodes:
+ * counters header, the FP64-path node list and the re-advection mark set.  The workspace must
+ * be 256-byte aligned.  Its contents need no initialisation; each call clears what it uses. */
+size_t ftle_workspace_bytes(int64_t n_nodes);
+
+/* --------------------------------------------------------------------------- single problem */
+
+/* Flowmap by RK4 (the input of the FTLE core, Section 2.2).
+ *   flowmap     device out, ftle_flowmap_bytes(dim, n, precision) bytes, layout per precision.
+ *   checkpoints nullable device out: the state every ckpt_every steps for the adjoint
+ *               (ftle_backward); ckpt_count = n_steps / ckpt_every + 1 slots of one
+ *               flowmap each (slot s holds the state after s * ckpt_every steps).
+ *   ckpt_every  > 0 when checkpoints is given, else ignored.
+ * Errors: FTLE_EINVAL (null mesh/flow/flowmap, dt = 0, T = 0, flow kind not valid for dim,
+ * coords precision not matching FP64 mode's need), FTLE_ERANGE (more than 2^31 - 1 steps). */
+int ftle_advect(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double T, double dt,
+                int32_t precision, void* flowmap, void* checkpoints, int32_t ckpt_every,
+                const ftle_options* opt, void* stream);
+
+/* The FTLE core (Section 2.1, Table 1) over the CSR neighbour lists (Section 2.2).
+ *   flowmap     device in (as written by ftle_advect for the same precision).
+ *   ftle_out    device out [n_nodes]: float, or double for FTLE_PREC_FP64.  NaN where the
+ *               neighbourhood is rank-deficient (fewer than dim neighbours, or
+ *               det(M) <= 1e-12 (tr(M)/dim)^dim with M = sum dx dx^T).
+ *   lambda_out  nullable device out [n_nodes] double: lambda_max of C.
+ *   workspace   device, ftle_workspace_bytes(n_nodes) bytes (required).
+ * For FP32/FP32C the gradient runs in float; nodes where float loses the result (lambda_max
+ * close to 1, two nearly equal top eigenvalues in 3D, an ill-conditioned M) are listed in the
+ * workspace and recomputed in FP64 by a second kernel in the same call. */
+int ftle_gradient_eig(const ftle_mesh* mesh, const void* flowmap, int32_t precision, double T,
+                      void* ftle_out, double* lambda_out, void* workspace, size_t workspace_bytes,
+                      const ftle_options* opt, void* stream);
+
+/* FP32C only (no-op for other precisions): re-advects in FP64 the nodes listed by the last
+ * ftle_gradient_eig on this workspace together with their neighbours, writes their flowmap
+ * back as exact (hi, lo) pairs, and recomputes the listed nodes' FTLE in FP64.  Must follow
+ * ftle_gradient_eig on the same stream, mesh, flowmap and workspace. */
+int ftle_refine(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double T, double dt,
+                int32_t precision, void* flowmap, void* ftle_out, double* lambda_out,
+                void* workspace, size_t workspace_bytes, const ftle_options* opt, void* stream);
+
+/* Whole path: ftle_advect, ftle_gradient_eig, then ftle_refine (FP32C).  flowmap is a caller
+ * buffer of ftle_flowmap_bytes bytes, left holding the (refined) flowmap. */
+int ftle_compute(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double T, double dt,
+                 int32_t precision, void* flowmap, void* ftle_out, double* lambda_out,
+                 void* workspace, size_t workspace_bytes, const ftle_options* opt, void* stream);
+
+/* End-to-end from HOST buffers: copies coords (float, or double for FP64), row_ptr and col_idx
+ * from host memory into `device_ws`, runs ftle_compute, copies the FTLE field back into
+ * ftle_host (float, or double for FP64) and synchronises `stream` before returning.
+ * Host buffers should be pinned for full copy bandwidth.  device_ws must hold
+ * ftle_host_workspace_bytes(dim, n_nodes, nnz, precision) bytes. */
+size_t ftle_host_workspace_bytes(int32_t dim, int64_t n_nodes, int64_t nnz, int32_t precision);
+int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coords_host,
+                      const int32_t* row_ptr_host, const int32_t* col_idx_host,
+                      const ftle_flow* flow, double t0, double T, double dt, int32_t precision,
+                      void* ftle_host, void* device_ws, size_t device_ws_bytes,
+                      const ftle_options* opt, void* stream);
+
+/* Synchronous read of the counters at the start of `workspace` (waits for `stream`). */
+int ftle_read_counters(const void* workspace, ftle_counters* out, void* stream);
+
+/* ---------------------------------------------------------------------------------- batched */
+
+/* Many independent problems of uneven size and horizon in one launch sequence: one persistent
+ * advection kernel and one persistent gradient kernel walk a shared queue of (instance, tile)
+ * items ordered longest-first (LPT), followed by the FP64 fix-up of flagged nodes.  All
+ * instances share dt and precision (FP32 or FP32C); per-instance t0 = 0.
+ *   meshes, flows, T  HOST arrays [n_inst] (mesh pointers inside are device pointers).
+ *   ftle_out          HOST array [n_inst] of device float pointers [meshes[i].n_nodes].
+ *   workspace         device, ftle_batch_workspace_bytes(...) bytes, 256-byte aligned. */
+size_t ftle_batch_workspace_bytes(int32_t n_inst, const ftle_mesh* meshes, int32_t precision);
+int ftle_batch(int32_t n_inst, const ftle_mesh* meshes, const ftle_flow* flows, const double* T,
+               double dt, int32_t precision, void* const* ftle_out, void* workspace,
+               size_t workspace_bytes, const ftle_options* opt, void* stream);
+
+/* A batch captured once into a CUDA graph and replayed: create builds the queue, uploads it
+ * into the workspace and captures the kernels; launch replays the graph on `stream`; destroy
+ * frees the graph.  The buffers named at create time must stay valid while the plan lives. */
+typedef struct ftle_batch_plan ftle_batch_plan;
+int ftle_batch_plan_create(int32_t n_inst, const ftle_mesh* meshes, const ftle_flow* flows,
+                           const double* T, double dt, int32_t precision, void* const* ftle_out,
+                           void* workspace, size_t workspace_bytes, const ftle_options* opt,
+                           void* stream, ftle_batch_plan** plan);
+int ftle_batch_plan_launch(ftle_batch_plan* plan, void* stream);
+int ftle_batch_plan_destroy(ftle_batch_plan* plan);
+
+/* ----------------------------------------------------------------------------- differentiation */
+
+/* Reverse-mode derivative of L = sum_i dL_dftle[i] FTLE_i with respect to the double-gyre
+ * parameters (A, eps, omega), 2D, FP32/FP32C forward.  Steps: the adjoint of the FTLE map gives
+ * dL/dphi at every node (a gather over the symmetric adjacency; the CSR lists must be
+ * symmetric), then the discrete adjoint of the RK4 steps runs backward segment by segment,
+ * recomputing each segment's states from the checkpoints written by ftle_advect, and the
+ * per-step parameter terms are summed in FP64 in a fixed order (deterministic).
+ *   flowmap, checkpoints  as written by ftle_advect with the same arguments and ckpt_every.
+ *   dL_dftle              device float [n_nodes].
+ *   dL_dparams            device double [3] out.
+ *   workspace             ftle_backward_workspace_bytes(n_nodes, dim) bytes. */
+size_t ftle_backward_workspace_bytes(int64_t n_nodes, int32_t dim);
+int ftle_backward(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double T, double dt,
+                  int32_t precision, const void* flowmap, const void* checkpoints,
+                  int32_t ckpt_every, const float* dL_dftle, double* dL_dparams, void* workspace,
+                  size_t workspace_bytes, const ftle_options* opt, void* stream);
+
+/* ---------------------------------------------------------------------------------- misc */
+
+const char* ftle_status_string(int status);
+const char* ftle_last_error(void); /* message of the calling thread's last failing call */
+int ftle_version(void);            /* FTLE_API_VERSION */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTLE_H */

@@ -1,0 +1,309 @@
+// RK4 flowmap advection kernels (the flowmap that the FTLE core of arXiv 2408.02758 takes as
+// input, Section 2.2).  One thread integrates one node; the state stays in registers for all
+// steps.  Time-dependent coefficients of the double gyre are shared by every node of a step and
+// live in a shared-memory table, rebuilt per chunk of steps.
+#pragma once
+
+#include "common.cuh"
+
+namespace ftle {
+
+enum Prec { P64 = 0, P32 = 1, P32C = 2 };
+enum Out { O64 = 0, O32 = 1, O32PAIR = 2 };
+
+constexpr int kAdvChunk = 2048;  // steps per coefficient-table chunk (2*chunk+1 half steps)
+
+struct AdvArgs {
+  int64_t n;                   // nodes (or list capacity when `list` is set)
+  const void* coords;          // SoA [dim][n_mesh], float or double
+  int64_t n_mesh;              // stride of coords / out
+  void* out;                   // flowmap, layout per Out
+  void* ckpt;                  // nullable: checkpoint slots, each one flowmap
+  int64_t ckpt_stride_bytes;   // bytes per checkpoint slot
+  int ckpt_every;
+  int nsteps;
+  double t0, h;                // h signed
+  float h32, h2_32, h6_32;     // h, h/2, h/6 rounded once
+  double p[12];                // flow parameters
+  const int32_t* list;         // nullable: process list[0 .. *list_count)
+  const unsigned long long* list_count;
+};
+
+// ------------------------------------------------------------------------- velocity dispatch
+
+template <int KIND, int DIM>
+__device__ __forceinline__ void vel_f32(const AdvArgs& a, const float* x, float ca, float cb, float* u) {
+  if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE) {
+    dg_vel32((float)(kPi * a.p[0]), ca, cb, x[0], x[1], u[0], u[1]);
+  } else if constexpr (KIND == FTLE_FLOW_ABC) {
+    abc_vel32((float)a.p[0], (float)a.p[1], (float)a.p[2], x[0], x[1], x[2], u[0], u[1], u[2]);
+  } else if constexpr (KIND == FTLE_FLOW_LINEAR) {
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      float s = 0.f;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) s = fmaf((float)a.p[r * DIM + c], x[c], s);
+      u[r] = s;
+    }
+  } else {
+    u[0] = x[0];
+    u[1] = -x[1];
+    if constexpr (DIM == 3) u[2] = 0.f;
+  }
+}
+
+template <int KIND, int DIM>
+__device__ __forceinline__ void vel_f32c(const AdvArgs& a, const float* xh, const float* xl, float ca,
+                                         float cbh, float cbl, float* u) {
+  if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE) {
+    dg_vel32c((float)(kPi * a.p[0]), ca, cbh, cbl, xh[0], xl[0], xh[1], xl[1], u[0], u[1]);
+  } else if constexpr (KIND == FTLE_FLOW_ABC) {
+    abc_vel32c((float)a.p[0], (float)a.p[1], (float)a.p[2], xh[0], xl[0], xh[1], xl[1], xh[2], xl[2],
+               u[0], u[1], u[2]);
+  } else if constexpr (KIND == FTLE_FLOW_LINEAR) {
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      float s = 0.f;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        float m = (float)a.p[r * DIM + c];
+        s = fmaf(m, xh[c], fmaf(m, xl[c], s));
+      }
+      u[r] = s;
+    }
+  } else {
+    u[0] = xh[0] + xl[0];
+    u[1] = -(xh[1] + xl[1]);
+    if constexpr (DIM == 3) u[2] = 0.f;
+  }
+}
+
+template <int KIND, int DIM>
+__device__ __forceinline__ void vel_f64(const AdvArgs& a, const double* x, double s_om, double* u) {
+  if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE) {
+    double A = a.p[0], eps = a.p[1];
+    double aa = eps * s_om, bb = 1.0 - 2.0 * eps * s_om;
+    double f = fma(aa, x[0], bb) * x[0];
+    double fx = fma(2.0 * aa, x[0], bb);
+    double sf, cf, sy, cy;
+    sincospi(f, &sf, &cf);
+    sincospi(x[1], &sy, &cy);
+    u[0] = -kPi * A * sf * cy;
+    u[1] = kPi * A * cf * sy * fx;
+  } else if constexpr (KIND == FTLE_FLOW_ABC) {
+    abc_vel64(a.p[0], a.p[1], a.p[2], x[0], x[1], x[2], u[0], u[1], u[2]);
+  } else if constexpr (KIND == FTLE_FLOW_LINEAR) {
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      double s = 0.0;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) s = fma(a.p[r * DIM + c], x[c], s);
+      u[r] = s;
+    }
+  } else {
+    u[0] = x[0];
+    u[1] = -x[1];
+    if constexpr (DIM == 3) u[2] = 0.0;
+  }
+}
+
+// ----------------------------------------------------------------------------- load / store
+
+template <typename CT>
+__device__ __forceinline__ double load_coord(const void* c, int64_t idx) {
+  return (double)__ldg(reinterpret_cast<const CT*>(c) + idx);
+}
+
+template <int OUT, int DIM>
+__device__ __forceinline__ void store_state(void* base, int64_t n, int64_t i, const float* xh,
+                                            const float* xl, const double* xd) {
+  if constexpr (OUT == O64) {
+    double* o = reinterpret_cast<double*>(base);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o[d * n + i] = xd[d];
+  } else if constexpr (OUT == O32) {
+    float* o = reinterpret_cast<float*>(base);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o[d * n + i] = xh[d];
+  } else {
+    float2* o = reinterpret_cast<float2*>(base);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o[d * n + i] = make_float2(xh[d], xl[d]);
+  }
+}
+
+// --------------------------------------------------------------------------------- kernel
+
+template <int KIND, int DIM, int PREC, int OUT, typename CT>
+__global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool kTable = (KIND == FTLE_FLOW_DOUBLE_GYRE);
+  float2* tab32 = reinterpret_cast<float2*>(smem_raw);
+  double* tab64 = reinterpret_cast<double*>(smem_raw);
+
+  const int64_t count = a.list ? (int64_t)*a.list_count : a.n;
+  const int nchunks = (a.nsteps + kAdvChunk - 1) / kAdvChunk;
+  const double nu = a.p[2] / kPi;  // omega / pi (double gyre)
+  bool table_valid = false;        // single-chunk tables are built once per block
+
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t slot = base + threadIdx.x;
+    const bool active = slot < count;
+    const int64_t i = active ? (a.list ? (int64_t)a.list[slot] : slot) : 0;
+
+    float xh[DIM], xl[DIM];
+    double xd[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      double c = active ? load_coord<CT>(a.coords, d * a.n_mesh + i) : 0.0;
+      xd[d] = c;
+      xh[d] = (float)c;
+      xl[d] = (float)(c - (double)xh[d]);
+    }
+    if (a.ckpt && active) {
+      store_state<OUT, DIM>(a.ckpt, a.n_mesh, i, xh, xl, xd);
+    }
+    int ck_left = a.ckpt_every;
+    int ck_slot = 1;
+
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int k0 = ch * kAdvChunk;
+      const int k1 = min(a.nsteps, k0 + kAdvChunk);
+      if constexpr (kTable) {
+        if (!(table_valid && nchunks == 1)) {
+          __syncthreads();
+          for (int m = threadIdx.x; m <= 2 * (k1 - k0); m += blockDim.x) {
+            if constexpr (PREC == P64) {
+              tab64[m] = sin(a.p[2] * (a.t0 + 0.5 * a.h * (double)(2 * k0 + m)));
+            } else {
+              tab32[m] = dg_coef(a.p[1], nu, a.t0, 0.5 * a.h, 2 * k0 + m);
+            }
+          }
+          __syncthreads();
+          table_valid = true;
+        }
+      }
+      if (!active) continue;
+      for (int k = k0; k < k1; ++k) {
+        const int m = 2 * (k - k0);
+        if constexpr (PREC == P64) {
+          double s0 = 0, s1 = 0, s2 = 0;
+          if constexpr (kTable) {
+            s0 = tab64[m];
+            s1 = tab64[m + 1];
+            s2 = tab64[m + 2];
+          }
+          double k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], y[DIM];
+          vel_f64<KIND, DIM>(a, xd, s0, k1v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) y[d] = fma(0.5 * a.h, k1v[d], xd[d]);
+          vel_f64<KIND, DIM>(a, y, s1, k2v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) y[d] = fma(0.5 * a.h, k2v[d], xd[d]);
+          vel_f64<KIND, DIM>(a, y, s1, k3v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) y[d] = fma(a.h, k3v[d], xd[d]);
+          vel_f64<KIND, DIM>(a, y, s2, k4v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d)
+            xd[d] += (a.h / 6.0) * (k1v[d] + 2.0 * (k2v[d] + k3v[d]) + k4v[d]);
+        } else if constexpr (PREC == P32) {
+          float c0a = 0, c0b = 0, c1a = 0, c1b = 0, c2a = 0, c2b = 0;
+          if constexpr (kTable) {
+            float2 t0 = tab32[m], t1 = tab32[m + 1], t2 = tab32[m + 2];
+            c0a = t0.x; c0b = fmaf(-2.f, t0.x, 1.f);
+            c1a = t1.x; c1b = fmaf(-2.f, t1.x, 1.f);
+            c2a = t2.x; c2b = fmaf(-2.f, t2.x, 1.f);
+          }
+          float k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], y[DIM];
+          vel_f32<KIND, DIM>(a, xh, c0a, c0b, k1v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) y[d] = fmaf(a.h2_32, k1v[d], xh[d]);
+          vel_f32<KIND, DIM>(a, y, c1a, c1b, k2v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) y[d] = fmaf(a.h2_32, k2v[d], xh[d]);
+          vel_f32<KIND, DIM>(a, y, c1a, c1b, k3v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) y[d] = fmaf(a.h32, k3v[d], xh[d]);
+          vel_f32<KIND, DIM>(a, y, c2a, c2b, k4v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d)
+            xh[d] = fmaf(a.h6_32, fmaf(2.f, k2v[d] + k3v[d], k1v[d] + k4v[d]), xh[d]);
+        } else {  // P32C
+          float c0a = 0, c0h = 0, c0l = 0, c1a = 0, c1h = 0, c1l = 0, c2a = 0, c2h = 0, c2l = 0;
+          if constexpr (kTable) {
+            float2 t0 = tab32[m], t1 = tab32[m + 1], t2 = tab32[m + 2];
+            c0a = t0.x; c0h = fmaf(-2.f, t0.x, 1.f); c0l = t0.y;
+            c1a = t1.x; c1h = fmaf(-2.f, t1.x, 1.f); c1l = t1.y;
+            c2a = t2.x; c2h = fmaf(-2.f, t2.x, 1.f); c2l = t2.y;
+          }
+          float k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], yh[DIM], yl[DIM];
+          vel_f32c<KIND, DIM>(a, xh, xl, c0a, c0h, c0l, k1v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            float e;
+            two_sum(xh[d], a.h2_32 * k1v[d], yh[d], e);
+            yl[d] = e + xl[d];
+          }
+          vel_f32c<KIND, DIM>(a, yh, yl, c1a, c1h, c1l, k2v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            float e;
+            two_sum(xh[d], a.h2_32 * k2v[d], yh[d], e);
+            yl[d] = e + xl[d];
+          }
+          vel_f32c<KIND, DIM>(a, yh, yl, c1a, c1h, c1l, k3v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            float e;
+            two_sum(xh[d], a.h32 * k3v[d], yh[d], e);
+            yl[d] = e + xl[d];
+          }
+          vel_f32c<KIND, DIM>(a, yh, yl, c2a, c2h, c2l, k4v);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            float inc = a.h6_32 * fmaf(2.f, k2v[d] + k3v[d], k1v[d] + k4v[d]);
+            float s, e;
+            two_sum(xh[d], inc + xl[d], s, e);
+            xh[d] = s;
+            xl[d] = e;
+          }
+        }
+        if (a.ckpt) {
+          if (--ck_left == 0) {
+            ck_left = a.ckpt_every;
+            if constexpr (PREC == P64) {
+#pragma unroll
+              for (int d = 0; d < DIM; ++d) {
+                xh[d] = (float)xd[d];
+                xl[d] = (float)(xd[d] - (double)xh[d]);
+              }
+            }
+            store_state<OUT, DIM>(reinterpret_cast<char*>(a.ckpt) + (int64_t)ck_slot * a.ckpt_stride_bytes,
+                                  a.n_mesh, i, xh, xl, xd);
+            ++ck_slot;
+          }
+        }
+      }
+    }
+    if (active) {
+      if constexpr (PREC == P64) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          xh[d] = (float)xd[d];
+          xl[d] = (float)(xd[d] - (double)xh[d]);
+        }
+      }
+      store_state<OUT, DIM>(a.out, a.n_mesh, i, xh, xl, xd);
+    }
+  }
+}
+
+// Host-side launcher (advect.cu): picks the instantiation for (kind, dim, prec, out, coord type).
+int launch_advect(int kind, int dim, int prec, int out, bool coord64, const AdvArgs& args, int grid,
+                  int block, cudaStream_t stream);
+
+size_t advect_smem_bytes(int kind, int prec, int nsteps);
+
+}  // namespace ftle

@@ -1,0 +1,446 @@
+// C-ABI of libftle.so (include/ftle.h): argument validation, workspace layout, launch sizing and
+// the sequence of kernels behind each entry point.  No exception crosses this boundary and no
+// device memory is allocated here.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "advect.cuh"
+#include "capi_internal.cuh"
+#include "gradient.cuh"
+
+namespace ftle {
+
+// ------------------------------------------------------------------------------------ status
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+int fail(int status, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+int cuda_fail(cudaError_t err, const char* where) {
+  snprintf(g_err, sizeof g_err, "%s: %s (%s)", where, cudaGetErrorName(err), cudaGetErrorString(err));
+  return FTLE_ECUDA;
+}
+
+int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+  if (dev < 64) {
+    int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
+
+WsLayout ws_layout(int64_t n) {
+  WsLayout L;
+  size_t off = 0;
+  L.header = off;
+  off += align256(sizeof(ftle_counters));
+  L.flag_list = off;
+  off += align256(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  L.mark_list = off;
+  off += align256(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  L.bitmap = off;
+  off += align256(sizeof(uint32_t) * (size_t)((n + 31) / 32 + 1));
+  L.total = off;
+  return L;
+}
+
+// ----------------------------------------------------------------------------- validation
+
+int check_mesh(const ftle_mesh* m) {
+  if (!m) return fail(FTLE_EINVAL, "mesh is NULL");
+  if (m->dim != 2 && m->dim != 3) return fail(FTLE_EINVAL, "mesh dim %d not in {2, 3}", m->dim);
+  if (m->n_nodes < 0 || m->n_nodes >= (int64_t)INT32_MAX)
+    return fail(FTLE_ERANGE, "n_nodes %lld outside [0, 2^31 - 1)", (long long)m->n_nodes);
+  if (m->nnz < 0 || m->nnz >= (int64_t)INT32_MAX)
+    return fail(FTLE_ERANGE, "nnz %lld outside [0, 2^31 - 1)", (long long)m->nnz);
+  if (m->coord_fp64 != 0 && m->coord_fp64 != 1) return fail(FTLE_EINVAL, "coord_fp64 must be 0 or 1");
+  if (m->n_nodes > 0 && (!m->coords || !m->row_ptr)) return fail(FTLE_EINVAL, "mesh pointers are NULL");
+  if (m->nnz > 0 && !m->col_idx) return fail(FTLE_EINVAL, "col_idx is NULL");
+  return FTLE_OK;
+}
+
+int check_flow(const ftle_flow* f, int dim) {
+  if (!f) return fail(FTLE_EINVAL, "flow is NULL");
+  if (f->reserved != 0) return fail(FTLE_EINVAL, "flow.reserved must be 0");
+  switch (f->kind) {
+    case FTLE_FLOW_DOUBLE_GYRE:
+      if (dim != 2) return fail(FTLE_EINVAL, "the double gyre is a 2D flow");
+      break;
+    case FTLE_FLOW_ABC:
+      if (dim != 3) return fail(FTLE_EINVAL, "the ABC flow is a 3D flow");
+      break;
+    case FTLE_FLOW_LINEAR:
+    case FTLE_FLOW_SADDLE:
+      break;
+    default:
+      return fail(FTLE_EINVAL, "unknown flow kind %d", f->kind);
+  }
+  for (int q = 0; q < 12; ++q)
+    if (!isfinite(f->p[q])) return fail(FTLE_EINVAL, "flow parameter %d is not finite", q);
+  return FTLE_OK;
+}
+
+int check_prec(int precision) {
+  if (precision != FTLE_PREC_FP64 && precision != FTLE_PREC_FP32 && precision != FTLE_PREC_FP32C)
+    return fail(FTLE_EINVAL, "unknown precision %d", precision);
+  return FTLE_OK;
+}
+
+int check_time(double T, double dt, int* nsteps) {
+  if (!isfinite(T) || T == 0.0) return fail(FTLE_EINVAL, "T must be finite and non-zero");
+  if (!isfinite(dt) || dt == 0.0) return fail(FTLE_EINVAL, "dt must be finite and non-zero");
+  const double ns = nearbyint(fabs(T) / fabs(dt));
+  if (!(ns >= 1.0)) return fail(FTLE_EINVAL, "|T| / |dt| rounds to zero steps");
+  if (ns > (double)INT32_MAX) return fail(FTLE_ERANGE, "step count %.0f beyond 2^31 - 1", ns);
+  *nsteps = (int)ns;
+  return FTLE_OK;
+}
+
+int check_workspace(const void* ws, size_t bytes, size_t need) {
+  if (!ws) return fail(FTLE_EWORKSPACE, "workspace is NULL");
+  if (((uintptr_t)ws & 255u) != 0) return fail(FTLE_EWORKSPACE, "workspace must be 256-byte aligned");
+  if (bytes < need) return fail(FTLE_EWORKSPACE, "workspace holds %zu bytes, needs %zu", bytes, need);
+  return FTLE_OK;
+}
+
+Launch resolve_launch(const ftle_options* opt) {
+  Launch L;
+  if (opt) {
+    if (opt->refine_mu != 0.0) L.refine_mu = opt->refine_mu;
+    if (opt->advect_block > 0) L.advect_block = opt->advect_block;
+    if (opt->advect_blocks_per_sm > 0) L.advect_bps = opt->advect_blocks_per_sm;
+    if (opt->grad_block > 0) L.grad_block = opt->grad_block;
+  }
+  return L;
+}
+
+int check_launch(const Launch& L) {
+  if (L.advect_block % 32 || L.advect_block < 32 || L.advect_block > 256)
+    return fail(FTLE_EINVAL, "advect_block must be a multiple of 32 in [32, 256]");
+  if (L.grad_block % 32 || L.grad_block < 32 || L.grad_block > 256)
+    return fail(FTLE_EINVAL, "grad_block must be a multiple of 32 in [32, 256]");
+  if (L.advect_bps < 1 || L.advect_bps > 64) return fail(FTLE_EINVAL, "advect_blocks_per_sm in [1, 64]");
+  return FTLE_OK;
+}
+
+size_t advect_smem_bytes(int kind, int prec, int nsteps) {
+  if (kind != FTLE_FLOW_DOUBLE_GYRE) return 0;
+  const int steps = nsteps < kAdvChunk ? nsteps : kAdvChunk;
+  const size_t entries = 2 * (size_t)steps + 1;
+  return entries * (prec == P64 ? sizeof(double) : sizeof(float2));
+}
+
+int launch_advect(int kind, int dim, int prec, int out, bool coord64, const AdvArgs& args, int grid,
+                  int block, cudaStream_t stream) {
+  const size_t smem = advect_smem_bytes(kind, prec, args.nsteps);
+  if (kind == FTLE_FLOW_DOUBLE_GYRE)
+    return launch_advect_dg(prec, out, coord64, args, grid, block, smem, stream);
+  if (kind == FTLE_FLOW_ABC) return launch_advect_abc(prec, out, coord64, args, grid, block, smem, stream);
+  return launch_advect_misc(kind, dim, prec, out, coord64, args, grid, block, smem, stream);
+}
+
+AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double T, double dt, int nsteps) {
+  AdvArgs a;
+  memset(&a, 0, sizeof a);
+  a.n = m->n_nodes;
+  a.n_mesh = m->n_nodes;
+  a.coords = m->coords;
+  a.nsteps = nsteps;
+  a.t0 = t0;
+  a.h = (T < 0 ? -1.0 : 1.0) * fabs(dt);
+  a.h32 = (float)a.h;
+  a.h2_32 = (float)(0.5 * a.h);
+  a.h6_32 = (float)(a.h / 6.0);
+  memcpy(a.p, f->p, sizeof a.p);
+  return a;
+}
+
+int grid_for(int64_t work, int block, int per_sm) {
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 1;
+  const int64_t need = (work + block - 1) / block;
+  const int64_t cap = (int64_t)sms * per_sm;
+  const int64_t g = need < cap ? need : cap;
+  return (int)(g > 0 ? g : 1);
+}
+
+GradArgs make_grad_args(const ftle_mesh* m, const void* phi, double T, void* ftle_out, double* lam_out,
+                        void* ws, const Launch& L) {
+  GradArgs g;
+  memset(&g, 0, sizeof g);
+  const WsLayout W = ws_layout(m->n_nodes);
+  char* w = reinterpret_cast<char*>(ws);
+  g.n = m->n_nodes;
+  g.coords = m->coords;
+  g.row_ptr = m->row_ptr;
+  g.col_idx = m->col_idx;
+  g.phi = phi;
+  g.ftle_out = ftle_out;
+  g.lam_out = lam_out;
+  g.inv_2absT = 1.0 / (2.0 * fabs(T));
+  g.refine_mu = (float)L.refine_mu;
+  g.hdr = reinterpret_cast<ftle_counters*>(w + W.header);
+  g.flag_list = reinterpret_cast<int32_t*>(w + W.flag_list);
+  return g;
+}
+
+int phi_layout_of(int precision) {
+  return precision == FTLE_PREC_FP64 ? PHI64 : (precision == FTLE_PREC_FP32 ? PHI32 : PHI32PAIR);
+}
+
+// One call of the gradient stage (float kernel + FP64 fix-up, or the FP64 kernel).
+int run_gradient(const ftle_mesh* m, const void* phi, int precision, double T, void* ftle_out,
+                 double* lam_out, void* ws, const Launch& L, cudaStream_t s) {
+  if (m->n_nodes == 0) return FTLE_OK;
+  GradArgs g = make_grad_args(m, phi, T, ftle_out, lam_out, ws, L);
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 1;
+  const bool c64 = m->coord_fp64 != 0;
+  if (precision == FTLE_PREC_FP64) {
+    const int grid = grid_for(m->n_nodes, 128, 16);
+    return launch_grad_f64(m->dim, PHI64, c64, true, g, grid, 128, s);
+  }
+  const int grid = grid_for(m->n_nodes, L.grad_block, 2048 / L.grad_block);
+  int rc = launch_grad_f32(m->dim, phi_layout_of(precision), c64, g, grid, L.grad_block, s);
+  if (rc) return rc;
+  GradArgs f = g;
+  f.list = g.flag_list;
+  f.list_count = &g.hdr->n_flagged;
+  return launch_grad_f64(m->dim, phi_layout_of(precision), c64, false, f, sms * 4, 128, s);
+}
+
+int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, double dt, int nsteps,
+               int precision, void* phi, void* ftle_out, double* lam_out, void* ws, const Launch& L,
+               cudaStream_t s) {
+  if (precision != FTLE_PREC_FP32C || m->n_nodes == 0 || L.refine_mu < 0) return FTLE_OK;
+  const WsLayout W = ws_layout(m->n_nodes);
+  char* w = reinterpret_cast<char*>(ws);
+  ftle_counters* hdr = reinterpret_cast<ftle_counters*>(w + W.header);
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 1;
+  FTLE_CUDA_CHECK(cudaMemsetAsync(w + W.bitmap, 0, sizeof(uint32_t) * (size_t)((m->n_nodes + 31) / 32 + 1), s));
+  FTLE_CUDA_CHECK(cudaMemsetAsync(&hdr->n_readvected, 0, sizeof(unsigned long long), s));
+  FTLE_CUDA_CHECK(cudaMemsetAsync(&hdr->n_degenerate, 0, sizeof(unsigned long long), s));
+  GradArgs g = make_grad_args(m, phi, T, ftle_out, lam_out, ws, L);
+  g.list = g.flag_list;
+  g.list_count = &hdr->n_flagged;
+  int32_t* mark = reinterpret_cast<int32_t*>(w + W.mark_list);
+  int rc = launch_refine_mark(g, mark, reinterpret_cast<uint32_t*>(w + W.bitmap), sms * 4, 128, s);
+  if (rc) return rc;
+  AdvArgs a = make_adv_args(m, fl, t0, T, dt, nsteps);
+  a.out = phi;
+  a.list = mark;
+  a.list_count = &hdr->n_readvected;
+  rc = launch_advect(fl->kind, m->dim, P64, O32PAIR, m->coord_fp64 != 0, a, sms * 2, 64, s);
+  if (rc) return rc;
+  return launch_grad_f64(m->dim, PHI32PAIR, m->coord_fp64 != 0, false, g, sms * 4, 128, s);
+}
+
+int run_advect(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, double dt, int nsteps,
+               int precision, void* phi, void* ckpt, int ckpt_every, const Launch& L, cudaStream_t s) {
+  if (m->n_nodes == 0) return FTLE_OK;
+  AdvArgs a = make_adv_args(m, fl, t0, T, dt, nsteps);
+  a.out = phi;
+  a.ckpt = ckpt;
+  a.ckpt_every = ckpt ? ckpt_every : 0;
+  a.ckpt_stride_bytes = (int64_t)ftle_flowmap_bytes(m->dim, m->n_nodes, precision);
+  const int prec = precision == FTLE_PREC_FP64 ? P64 : (precision == FTLE_PREC_FP32 ? P32 : P32C);
+  const int out = precision == FTLE_PREC_FP64 ? O64 : (precision == FTLE_PREC_FP32 ? O32 : O32PAIR);
+  int block = L.advect_block;
+  if (prec == P64 && block > 128) block = 128;
+  const int grid = grid_for(m->n_nodes, block, L.advect_bps * 256 / block);
+  return launch_advect(fl->kind, m->dim, prec, out, m->coord_fp64 != 0, a, grid, block, s);
+}
+
+}  // namespace ftle
+
+using namespace ftle;
+
+// =================================================================================== C-ABI
+
+extern "C" {
+
+int ftle_version(void) { return FTLE_API_VERSION; }
+
+const char* ftle_last_error(void) { return g_err; }
+
+const char* ftle_status_string(int status) {
+  switch (status) {
+    case FTLE_OK: return "ok";
+    case FTLE_EINVAL: return "invalid argument";
+    case FTLE_ECUDA: return "CUDA error";
+    case FTLE_EWORKSPACE: return "workspace missing, misaligned or too small";
+    case FTLE_EUNSUPPORTED: return "unsupported combination";
+    case FTLE_ERANGE: return "size beyond a fixed limit";
+    default: return "unknown status";
+  }
+}
+
+size_t ftle_flowmap_bytes(int32_t dim, int64_t n_nodes, int32_t precision) {
+  if ((dim != 2 && dim != 3) || n_nodes < 0) return 0;
+  const size_t per = precision == FTLE_PREC_FP32 ? sizeof(float) : (precision == FTLE_PREC_FP64 ||
+                                                                       precision == FTLE_PREC_FP32C)
+                                                                          ? 8
+                                                                          : 0;
+  return per * (size_t)dim * (size_t)n_nodes;
+}
+
+size_t ftle_workspace_bytes(int64_t n_nodes) {
+  if (n_nodes < 0) return 0;
+  return ws_layout(n_nodes).total;
+}
+
+int ftle_advect(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double T, double dt,
+                int32_t precision, void* flowmap, void* checkpoints, int32_t ckpt_every,
+                const ftle_options* opt, void* stream) {
+  int rc, nsteps = 0;
+  if ((rc = check_mesh(mesh)) || (rc = check_flow(flow, mesh->dim)) || (rc = check_prec(precision)) ||
+      (rc = check_time(T, dt, &nsteps)))
+    return rc;
+  if (!isfinite(t0)) return fail(FTLE_EINVAL, "t0 must be finite");
+  if (mesh->n_nodes > 0 && !flowmap) return fail(FTLE_EINVAL, "flowmap is NULL");
+  if (checkpoints && ckpt_every <= 0) return fail(FTLE_EINVAL, "ckpt_every must be > 0 with checkpoints");
+  const Launch L = resolve_launch(opt);
+  if ((rc = check_launch(L))) return rc;
+  return run_advect(mesh, flow, t0, T, dt, nsteps, precision, flowmap, checkpoints, ckpt_every, L,
+                    (cudaStream_t)stream);
+}
+
+int ftle_gradient_eig(const ftle_mesh* mesh, const void* flowmap, int32_t precision, double T,
+                      void* ftle_out, double* lambda_out, void* workspace, size_t workspace_bytes,
+                      const ftle_options* opt, void* stream) {
+  int rc;
+  if ((rc = check_mesh(mesh)) || (rc = check_prec(precision))) return rc;
+  if (!isfinite(T) || T == 0.0) return fail(FTLE_EINVAL, "T must be finite and non-zero");
+  if (mesh->n_nodes > 0 && (!flowmap || !ftle_out)) return fail(FTLE_EINVAL, "flowmap / ftle_out is NULL");
+  if ((rc = check_workspace(workspace, workspace_bytes, ftle_workspace_bytes(mesh->n_nodes)))) return rc;
+  const Launch L = resolve_launch(opt);
+  if ((rc = check_launch(L))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  FTLE_CUDA_CHECK(cudaMemsetAsync(workspace, 0, sizeof(ftle_counters), s));
+  return run_gradient(mesh, flowmap, precision, T, ftle_out, lambda_out, workspace, L, s);
+}
+
+int ftle_refine(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double T, double dt,
+                int32_t precision, void* flowmap, void* ftle_out, double* lambda_out, void* workspace,
+                size_t workspace_bytes, const ftle_options* opt, void* stream) {
+  int rc, nsteps = 0;
+  if ((rc = check_mesh(mesh)) || (rc = check_flow(flow, mesh->dim)) || (rc = check_prec(precision)) ||
+      (rc = check_time(T, dt, &nsteps)))
+    return rc;
+  if (mesh->n_nodes > 0 && (!flowmap || !ftle_out)) return fail(FTLE_EINVAL, "flowmap / ftle_out is NULL");
+  if ((rc = check_workspace(workspace, workspace_bytes, ftle_workspace_bytes(mesh->n_nodes)))) return rc;
+  const Launch L = resolve_launch(opt);
+  if ((rc = check_launch(L))) return rc;
+  return run_refine(mesh, flow, t0, T, dt, nsteps, precision, flowmap, ftle_out, lambda_out, workspace, L,
+                    (cudaStream_t)stream);
+}
+
+int ftle_compute(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double T, double dt,
+                 int32_t precision, void* flowmap, void* ftle_out, double* lambda_out, void* workspace,
+                 size_t workspace_bytes, const ftle_options* opt, void* stream) {
+  int rc, nsteps = 0;
+  if ((rc = check_mesh(mesh)) || (rc = check_flow(flow, mesh->dim)) || (rc = check_prec(precision)) ||
+      (rc = check_time(T, dt, &nsteps)))
+    return rc;
+  if (!isfinite(t0)) return fail(FTLE_EINVAL, "t0 must be finite");
+  if (mesh->n_nodes > 0 && (!flowmap || !ftle_out)) return fail(FTLE_EINVAL, "flowmap / ftle_out is NULL");
+  if ((rc = check_workspace(workspace, workspace_bytes, ftle_workspace_bytes(mesh->n_nodes)))) return rc;
+  const Launch L = resolve_launch(opt);
+  if ((rc = check_launch(L))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = run_advect(mesh, flow, t0, T, dt, nsteps, precision, flowmap, nullptr, 0, L, s))) return rc;
+  FTLE_CUDA_CHECK(cudaMemsetAsync(workspace, 0, sizeof(ftle_counters), s));
+  if ((rc = run_gradient(mesh, flowmap, precision, T, ftle_out, lambda_out, workspace, L, s))) return rc;
+  return run_refine(mesh, flow, t0, T, dt, nsteps, precision, flowmap, ftle_out, lambda_out, workspace, L, s);
+}
+
+size_t ftle_host_workspace_bytes(int32_t dim, int64_t n_nodes, int64_t nnz, int32_t precision) {
+  if ((dim != 2 && dim != 3) || n_nodes < 0 || nnz < 0) return 0;
+  const size_t cb = (precision == FTLE_PREC_FP64 ? sizeof(double) : sizeof(float)) * (size_t)dim * (size_t)n_nodes;
+  size_t off = align256(ftle_workspace_bytes(n_nodes));
+  off += align256(cb);                                               // coords
+  off += align256(sizeof(int32_t) * (size_t)(n_nodes + 1));          // row_ptr
+  off += align256(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));    // col_idx
+  off += align256(ftle_flowmap_bytes(dim, n_nodes, precision));      // flowmap
+  off += align256((precision == FTLE_PREC_FP64 ? 8 : 4) * (size_t)(n_nodes > 0 ? n_nodes : 1));  // ftle
+  return off;
+}
+
+int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coords_host,
+                      const int32_t* row_ptr_host, const int32_t* col_idx_host, const ftle_flow* flow,
+                      double t0, double T, double dt, int32_t precision, void* ftle_host, void* device_ws,
+                      size_t device_ws_bytes, const ftle_options* opt, void* stream) {
+  int rc;
+  if ((rc = check_prec(precision))) return rc;
+  if ((dim != 2 && dim != 3) || n_nodes < 0 || nnz < 0) return fail(FTLE_EINVAL, "bad dim / sizes");
+  if (n_nodes > 0 && (!coords_host || !row_ptr_host || !ftle_host)) return fail(FTLE_EINVAL, "host buffer is NULL");
+  if (nnz > 0 && !col_idx_host) return fail(FTLE_EINVAL, "col_idx_host is NULL");
+  const size_t need = ftle_host_workspace_bytes(dim, n_nodes, nnz, precision);
+  if ((rc = check_workspace(device_ws, device_ws_bytes, need))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* w = reinterpret_cast<char*>(device_ws);
+  const size_t cb = (precision == FTLE_PREC_FP64 ? sizeof(double) : sizeof(float)) * (size_t)dim * (size_t)n_nodes;
+  size_t off = align256(ftle_workspace_bytes(n_nodes));
+  char* coords = w + off;
+  off += align256(cb);
+  int32_t* rp = reinterpret_cast<int32_t*>(w + off);
+  off += align256(sizeof(int32_t) * (size_t)(n_nodes + 1));
+  int32_t* ci = reinterpret_cast<int32_t*>(w + off);
+  off += align256(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+  void* phi = w + off;
+  off += align256(ftle_flowmap_bytes(dim, n_nodes, precision));
+  void* ftle_dev = w + off;
+  const size_t ob = (precision == FTLE_PREC_FP64 ? 8 : 4) * (size_t)n_nodes;
+  if (n_nodes > 0) {
+    FTLE_CUDA_CHECK(cudaMemcpyAsync(coords, coords_host, cb, cudaMemcpyHostToDevice, s));
+    FTLE_CUDA_CHECK(cudaMemcpyAsync(rp, row_ptr_host, sizeof(int32_t) * (size_t)(n_nodes + 1),
+                                    cudaMemcpyHostToDevice, s));
+  }
+  if (nnz > 0) FTLE_CUDA_CHECK(cudaMemcpyAsync(ci, col_idx_host, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
+  ftle_mesh m;
+  m.dim = dim;
+  m.coord_fp64 = precision == FTLE_PREC_FP64 ? 1 : 0;
+  m.n_nodes = n_nodes;
+  m.nnz = nnz;
+  m.coords = coords;
+  m.row_ptr = rp;
+  m.col_idx = ci;
+  rc = ftle_compute(&m, flow, t0, T, dt, precision, phi, ftle_dev, nullptr, device_ws,
+                    align256(ftle_workspace_bytes(n_nodes)), opt, stream);
+  if (rc) return rc;
+  if (n_nodes > 0) FTLE_CUDA_CHECK(cudaMemcpyAsync(ftle_host, ftle_dev, ob, cudaMemcpyDeviceToHost, s));
+  FTLE_CUDA_CHECK(cudaStreamSynchronize(s));
+  return FTLE_OK;
+}
+
+int ftle_read_counters(const void* workspace, ftle_counters* out, void* stream) {
+  if (!workspace || !out) return fail(FTLE_EINVAL, "workspace / out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  FTLE_CUDA_CHECK(cudaMemcpyAsync(out, workspace, sizeof(ftle_counters), cudaMemcpyDeviceToHost, s));
+  FTLE_CUDA_CHECK(cudaStreamSynchronize(s));
+  return FTLE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,45 @@
+// Internal helpers shared by the C-ABI translation units (capi.cu, batch.cu, adjoint.cu).
+#pragma once
+
+#include "advect.cuh"
+#include "common.cuh"
+#include "gradient.cuh"
+
+namespace ftle {
+
+struct Launch {
+  double refine_mu = 0.1;
+  int advect_block = 256;
+  int advect_bps = 8;     // resident blocks per SM for 256-thread blocks (scaled for others)
+  int grad_block = 256;
+};
+
+int check_mesh(const ftle_mesh* m);
+int check_flow(const ftle_flow* f, int dim);
+int check_prec(int precision);
+int check_time(double T, double dt, int* nsteps);
+int check_workspace(const void* ws, size_t bytes, size_t need);
+Launch resolve_launch(const ftle_options* opt);
+int check_launch(const Launch& L);
+int grid_for(int64_t work, int block, int per_sm);
+int phi_layout_of(int precision);
+
+int launch_advect_dg(int prec, int out, bool coord64, const AdvArgs& args, int grid, int block,
+                     size_t smem, cudaStream_t stream);
+int launch_advect_abc(int prec, int out, bool coord64, const AdvArgs& args, int grid, int block,
+                      size_t smem, cudaStream_t stream);
+int launch_advect_misc(int kind, int dim, int prec, int out, bool coord64, const AdvArgs& args,
+                       int grid, int block, size_t smem, cudaStream_t stream);
+
+AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double T, double dt, int nsteps);
+GradArgs make_grad_args(const ftle_mesh* m, const void* phi, double T, void* ftle_out, double* lam_out,
+                        void* ws, const Launch& L);
+int run_advect(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, double dt, int nsteps,
+               int precision, void* phi, void* ckpt, int ckpt_every, const Launch& L, cudaStream_t s);
+int run_gradient(const ftle_mesh* m, const void* phi, int precision, double T, void* ftle_out,
+                 double* lam_out, void* ws, const Launch& L, cudaStream_t s);
+int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, double dt, int nsteps,
+               int precision, void* phi, void* ftle_out, double* lam_out, void* ws, const Launch& L,
+               cudaStream_t s);
+
+}  // namespace ftle

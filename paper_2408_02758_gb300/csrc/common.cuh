@@ -1,0 +1,169 @@
+// Shared device and host helpers of libftle.so (CUDA path only; nothing here is used by the
+// oracle).  Velocity fields, error-free float transformations and launch plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ftle.h"
+
+namespace ftle {
+
+// ------------------------------------------------------------------------------------ status
+
+void set_error(const char* fmt, ...);
+int fail(int status, const char* fmt, ...);
+int cuda_fail(cudaError_t err, const char* where);
+
+#define FTLE_CUDA_CHECK(expr)                                  \
+  do {                                                         \
+    cudaError_t _e = (expr);                                   \
+    if (_e != cudaSuccess) return ::ftle::cuda_fail(_e, #expr); \
+  } while (0)
+
+#define FTLE_LAUNCH_CHECK(where)                                 \
+  do {                                                           \
+    cudaError_t _e = cudaGetLastError();                         \
+    if (_e != cudaSuccess) return ::ftle::cuda_fail(_e, where);  \
+  } while (0)
+
+int device_sm_count();
+
+// Workspace layout shared by gradient_eig / refine / compute (all offsets 256-aligned).
+struct WsLayout {
+  size_t header = 0;     // ftle_counters
+  size_t flag_list = 0;  // int32 [n]
+  size_t mark_list = 0;  // int32 [n]
+  size_t bitmap = 0;     // uint32 [ceil(n/32)]
+  size_t total = 0;
+};
+WsLayout ws_layout(int64_t n);
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ------------------------------------------------------------------ error-free transformations
+
+// Knuth's TwoSum: s + e == a + b exactly (round-to-nearest, no reassociation).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// ------------------------------------------------------------------------------ flow params
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct FlowArgs {
+  int kind;
+  int dim;
+  double p[12];
+};
+
+// Double gyre time coefficients at the half steps t_m = t0 + m h/2: a(t) = eps sin(omega t)
+// rounded to float, and b = 1 - 2a carried as b_h + b_l with b_h = fl(1 - 2a) and b_l its exact
+// residual, so that 2a + b is exactly 1 and the walls x = 0, 2 stay invariant in float
+// arithmetic.  sin(omega t) = sin(pi u), u = (omega/pi) t formed and reduced to [-1/2, 1/2] in
+// double, then evaluated by sinpif: the argument keeps double accuracy, the value float.
+// Returns (a, b_l); b_h = fmaf(-2, a, 1).
+__device__ __forceinline__ float2 dg_coef(double eps, double nu, double t0, double half_h, int m) {
+  double u = nu * (t0 + half_h * (double)m);
+  double k = rint(u);
+  float s = sinpif((float)(u - k));
+  if (((long long)k) & 1) s = -s;  // sin(pi (k + r)) = (-1)^k sin(pi r)
+  float a = (float)eps * s;
+  float bh, bl;
+  two_sum(1.0f, -2.0f * a, bh, bl);
+  return make_float2(a, bl);
+}
+
+// --- double gyre, plain float: (u, v) at (x, y) with coefficients (a, b)
+__device__ __forceinline__ void dg_vel32(float piA, float a, float b, float x, float y, float& u,
+                                         float& v) {
+  float f = fmaf(a, x, b) * x;
+  float fx = fmaf(2.0f * a, x, b);
+  float sf, cf, sy, cy;
+  sincospif(f, &sf, &cf);
+  sincospif(y, &sy, &cy);
+  u = -piA * sf * cy;
+  v = piA * cf * sy * fx;
+}
+
+// --- double gyre at the compensated point (xh + xl, yh + yl).  f = x (a x + b) is formed with
+// error-free products and sums, so its rounding does not act as a position error; sin/cos of
+// pi (fh + fl) take the first-order correction pi fl cos / -pi fl sin.  b = bh + bl.
+__device__ __forceinline__ void dg_vel32c(float piA, float a, float bh, float bl, float xh, float xl,
+                                          float yh, float yl, float& u, float& v) {
+  const float kPiF = 3.14159265358979323846f;
+  float p = a * xh;
+  float pe = fmaf(a, xh, -p);  // a xh = p + pe exactly
+  float g, ge;
+  two_sum(p, bh, g, ge);       // p + bh = g + ge exactly
+  ge = ge + (bl + fmaf(a, xl, pe));  // a x + b = g + ge (to second order)
+  float fh = g * xh;
+  float fe = fmaf(g, xh, -fh);               // g xh = fh + fe exactly
+  float fl = fe + fmaf(ge, xh, g * xl);      // f = fh + fl
+  float fx = fmaf(2.0f * a, xh, bh + fmaf(2.0f * a, xl, bl));
+  float sf, cf, sy, cy;
+  sincospif(fh, &sf, &cf);
+  sincospif(yh, &sy, &cy);
+  float df = kPiF * fl, dy = kPiF * yl;
+  float sf2 = fmaf(df, cf, sf), cf2 = fmaf(-df, sf, cf);
+  float sy2 = fmaf(dy, cy, sy), cy2 = fmaf(-dy, sy, cy);
+  u = -piA * sf2 * cy2;
+  v = piA * cf2 * sy2 * fx;
+}
+
+// --- double gyre, double precision
+__device__ __forceinline__ void dg_vel64(double A, double eps, double om, double t, double x,
+                                         double y, double& u, double& v) {
+  double s = sin(om * t);
+  double a = eps * s, b = 1.0 - 2.0 * eps * s;
+  double f = fma(a, x, b) * x;
+  double fx = fma(2.0 * a, x, b);
+  double sf, cf, sy, cy;
+  sincospi(f, &sf, &cf);
+  sincospi(y, &sy, &cy);
+  u = -kPi * A * sf * cy;
+  v = kPi * A * cf * sy * fx;
+}
+
+// --- ABC flow
+__device__ __forceinline__ void abc_vel32(float A, float B, float C, float x, float y, float z,
+                                          float& u, float& v, float& w) {
+  float sx, cx, sy, cy, sz, cz;
+  sincosf(x, &sx, &cx);
+  sincosf(y, &sy, &cy);
+  sincosf(z, &sz, &cz);
+  u = fmaf(A, sz, C * cy);
+  v = fmaf(B, sx, A * cz);
+  w = fmaf(C, sy, B * cx);
+}
+
+__device__ __forceinline__ void abc_vel32c(float A, float B, float C, float xh, float xl, float yh,
+                                           float yl, float zh, float zl, float& u, float& v,
+                                           float& w) {
+  float sx, cx, sy, cy, sz, cz;
+  sincosf(xh, &sx, &cx);
+  sincosf(yh, &sy, &cy);
+  sincosf(zh, &sz, &cz);
+  float sx2 = fmaf(xl, cx, sx), cx2 = fmaf(-xl, sx, cx);
+  float sy2 = fmaf(yl, cy, sy), cy2 = fmaf(-yl, sy, cy);
+  float sz2 = fmaf(zl, cz, sz), cz2 = fmaf(-zl, sz, cz);
+  u = fmaf(A, sz2, C * cy2);
+  v = fmaf(B, sx2, A * cz2);
+  w = fmaf(C, sy2, B * cx2);
+}
+
+__device__ __forceinline__ void abc_vel64(double A, double B, double C, double x, double y, double z,
+                                          double& u, double& v, double& w) {
+  double sx, cx, sy, cy, sz, cz;
+  sincos(x, &sx, &cx);
+  sincos(y, &sy, &cy);
+  sincos(z, &sz, &cz);
+  u = fma(A, sz, C * cy);
+  v = fma(B, sx, A * cz);
+  w = fma(C, sy, B * cx);
+}
+
+}  // namespace ftle

@@ -1,0 +1,42 @@
+// FTLE core kernels: least-squares flowmap gradient over each node's CSR neighbour list, the
+// Cauchy-Green tensor, its largest eigenvalue and the FTLE (arXiv 2408.02758, Section 2.1 and
+// Table 1: the per-point core; Section 2.2: precomputed neighbour lists and the branch-reduced
+// gradient).  The float kernel handles every node; the nodes where float cancels are listed
+// and recomputed by the double kernel.
+#pragma once
+
+#include "common.cuh"
+
+namespace ftle {
+
+enum PhiLayout { PHI64 = 0, PHI32 = 1, PHI32PAIR = 2 };
+
+struct GradArgs {
+  int64_t n;                   // nodes of the mesh
+  const void* coords;          // SoA [dim][n], float or double
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const void* phi;             // flowmap, layout per PhiLayout
+  void* ftle_out;              // float [n] (double [n] when out64)
+  double* lam_out;             // nullable
+  double inv_2absT;            // 1 / (2 |T|)
+  float refine_mu;             // float kernel: flag nodes with lambda_max - 1 < refine_mu
+  ftle_counters* hdr;
+  int32_t* flag_list;          // float kernel appends here
+  const int32_t* list;         // double kernel: nullable node list ...
+  const unsigned long long* list_count;  // ... and its device-side length
+};
+
+// Conditioning and cancellation thresholds of the float kernel (see gradient.cu).
+constexpr float kCondFlag = 0.02f;       // det(M) <= kCondFlag (tr M / d)^d -> FP64 path
+constexpr float kNearDoubleTop = 1e-3f;  // 3D: 1 + r <= this (two top eigenvalues close) -> FP64
+constexpr double kRankTol = 1e-12;       // FP64: det(M) <= kRankTol (tr M / d)^d -> rank-deficient
+
+int launch_grad_f32(int dim, int phi_layout, bool coord64, const GradArgs& a, int grid, int block,
+                    cudaStream_t stream);
+int launch_grad_f64(int dim, int phi_layout, bool coord64, bool out64, const GradArgs& a, int grid,
+                    int block, cudaStream_t stream);
+int launch_refine_mark(const GradArgs& a, int32_t* mark_list, uint32_t* bitmap, int grid, int block,
+                       cudaStream_t stream);
+
+}  // namespace ftle

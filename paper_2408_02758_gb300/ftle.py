@@ -1,0 +1,312 @@
+"""Python binding of libftle.so (``include/ftle.h``): the same entry points, argument marshalling only.
+
+Device memory and streams come from PyTorch; every step of the path runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library cannot be built or loaded, or a call fails, an
+exception is raised.
+
+Typical use::
+
+    from paper_2408_02758_gb300 import ftle, inputs
+    w = inputs.preset(1)                       # 2048 x 1024 jittered triangle mesh, double gyre
+    dm = ftle.DeviceMesh.from_mesh(w.mesh)     # coords / CSR to the GPU
+    out = ftle.compute(dm, w.flow, w.T, w.dt, "fp32c")   # FTLE field (torch tensor on the GPU)
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, Structure, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_uint64, c_void_p
+
+import numpy as np
+
+from . import _build
+
+PREC = {"fp64": 0, "fp32": 1, "fp32c": 2}
+FTLE_OK, FTLE_EINVAL, FTLE_ECUDA, FTLE_EWORKSPACE, FTLE_EUNSUPPORTED, FTLE_ERANGE = 0, -1, -2, -3, -4, -5
+
+
+class ftle_mesh(Structure):
+    _fields_ = [("dim", c_int32), ("coord_fp64", c_int32), ("n_nodes", c_int64), ("nnz", c_int64),
+                ("coords", c_void_p), ("row_ptr", c_void_p), ("col_idx", c_void_p)]
+
+
+class ftle_flow(Structure):
+    _fields_ = [("kind", c_int32), ("reserved", c_int32), ("p", c_double * 12)]
+
+
+class ftle_counters(Structure):
+    _fields_ = [("n_flagged", c_uint64), ("n_degenerate", c_uint64), ("n_readvected", c_uint64),
+                ("reserved", c_uint64 * 5)]
+
+
+class ftle_options(Structure):
+    _fields_ = [("refine_mu", c_double), ("advect_block", c_int32), ("advect_blocks_per_sm", c_int32),
+                ("grad_block", c_int32), ("grad_tile", c_int32), ("reserved", c_int32 * 4)]
+
+
+class FTLEError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn} failed with status {status}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+# (name, restype, argtypes) of every entry point in include/ftle.h
+_SIGS = [
+    ("ftle_version", c_int, []),
+    ("ftle_last_error", c_char_p, []),
+    ("ftle_status_string", c_char_p, [c_int]),
+    ("ftle_flowmap_bytes", c_size_t, [c_int32, c_int64, c_int32]),
+    ("ftle_workspace_bytes", c_size_t, [c_int64]),
+    ("ftle_advect", c_int, [POINTER(ftle_mesh), POINTER(ftle_flow), c_double, c_double, c_double, c_int32,
+                            c_void_p, c_void_p, c_int32, POINTER(ftle_options), c_void_p]),
+    ("ftle_gradient_eig", c_int, [POINTER(ftle_mesh), c_void_p, c_int32, c_double, c_void_p, c_void_p,
+                                  c_void_p, c_size_t, POINTER(ftle_options), c_void_p]),
+    ("ftle_refine", c_int, [POINTER(ftle_mesh), POINTER(ftle_flow), c_double, c_double, c_double, c_int32,
+                            c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, POINTER(ftle_options), c_void_p]),
+    ("ftle_compute", c_int, [POINTER(ftle_mesh), POINTER(ftle_flow), c_double, c_double, c_double, c_int32,
+                             c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, POINTER(ftle_options), c_void_p]),
+    ("ftle_host_workspace_bytes", c_size_t, [c_int32, c_int64, c_int64, c_int32]),
+    ("ftle_compute_host", c_int, [c_int32, c_int64, c_int64, c_void_p, c_void_p, c_void_p, POINTER(ftle_flow),
+                                  c_double, c_double, c_double, c_int32, c_void_p, c_void_p, c_size_t,
+                                  POINTER(ftle_options), c_void_p]),
+    ("ftle_read_counters", c_int, [c_void_p, POINTER(ftle_counters), c_void_p]),
+    ("ftle_batch_workspace_bytes", c_size_t, [c_int32, POINTER(ftle_mesh), c_int32]),
+    ("ftle_batch", c_int, [c_int32, POINTER(ftle_mesh), POINTER(ftle_flow), POINTER(c_double), c_double, c_int32,
+                           POINTER(c_void_p), c_void_p, c_size_t, POINTER(ftle_options), c_void_p]),
+    ("ftle_batch_plan_create", c_int, [c_int32, POINTER(ftle_mesh), POINTER(ftle_flow), POINTER(c_double),
+                                       c_double, c_int32, POINTER(c_void_p), c_void_p, c_size_t,
+                                       POINTER(ftle_options), c_void_p, POINTER(c_void_p)]),
+    ("ftle_batch_plan_launch", c_int, [c_void_p, c_void_p]),
+    ("ftle_batch_plan_destroy", c_int, [c_void_p]),
+    ("ftle_backward_workspace_bytes", c_size_t, [c_int64, c_int32]),
+    ("ftle_backward", c_int, [POINTER(ftle_mesh), POINTER(ftle_flow), c_double, c_double, c_double, c_int32,
+                              c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_size_t,
+                              POINTER(ftle_options), c_void_p]),
+]
+
+
+def lib():
+    """Load (building first if its sources changed) libftle.so; raise if that is impossible."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build_ftle()
+        L = ctypes.CDLL(str(path))
+        for name, res, args in _SIGS:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def library_path() -> str:
+    return str(_build.LIBFTLE)
+
+
+def _check(fn: str, rc: int):
+    if rc != FTLE_OK:
+        msg = lib().ftle_last_error().decode(errors="replace")
+        raise FTLEError(fn, rc, msg)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _prec(p) -> int:
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def make_flow(flow) -> ftle_flow:
+    """ftle_flow from an ``inputs.FlowSpec`` (or anything with ``kind`` and ``params``)."""
+    f = ftle_flow()
+    f.kind = int(flow.kind)
+    f.reserved = 0
+    p = np.zeros(12)
+    src = np.asarray(flow.params, dtype=np.float64).reshape(-1)
+    p[: src.size] = src
+    for q in range(12):
+        f.p[q] = float(p[q])
+    return f
+
+
+def make_options(refine_mu: float = 0.0, advect_block: int = 0, advect_blocks_per_sm: int = 0,
+                 grad_block: int = 0, grad_tile: int = 0) -> ftle_options:
+    o = ftle_options()
+    o.refine_mu = refine_mu
+    o.advect_block = advect_block
+    o.advect_blocks_per_sm = advect_blocks_per_sm
+    o.grad_block = grad_block
+    o.grad_tile = grad_tile
+    return o
+
+
+class DeviceMesh:
+    """Mesh arrays resident on the GPU plus the ``ftle_mesh`` descriptor that points at them."""
+
+    def __init__(self, coords, row_ptr, col_idx):
+        import torch
+
+        assert coords.is_cuda and row_ptr.is_cuda and col_idx.is_cuda
+        assert coords.dtype in (torch.float32, torch.float64)
+        assert row_ptr.dtype == torch.int32 and col_idx.dtype == torch.int32
+        self.coords = coords.contiguous()
+        self.row_ptr = row_ptr.contiguous()
+        self.col_idx = col_idx.contiguous()
+        d = ftle_mesh()
+        d.dim = int(self.coords.shape[0])
+        d.coord_fp64 = 1 if self.coords.dtype == torch.float64 else 0
+        d.n_nodes = int(self.coords.shape[1])
+        d.nnz = int(self.col_idx.numel())
+        d.coords = _ptr(self.coords)
+        d.row_ptr = _ptr(self.row_ptr)
+        d.col_idx = _ptr(self.col_idx) if d.nnz else None
+        self.desc = d
+
+    @staticmethod
+    def from_mesh(mesh, device="cuda"):
+        import torch
+
+        return DeviceMesh(torch.from_numpy(np.ascontiguousarray(mesh.coords)).to(device),
+                          torch.from_numpy(mesh.row_ptr).to(device), torch.from_numpy(mesh.col_idx).to(device))
+
+    @property
+    def dim(self) -> int:
+        return self.desc.dim
+
+    @property
+    def n_nodes(self) -> int:
+        return self.desc.n_nodes
+
+
+# ------------------------------------------------------------------------------ raw entry points
+
+
+def ftle_version() -> int:
+    return int(lib().ftle_version())
+
+
+def ftle_flowmap_bytes(dim: int, n_nodes: int, precision) -> int:
+    return int(lib().ftle_flowmap_bytes(dim, n_nodes, _prec(precision)))
+
+
+def ftle_workspace_bytes(n_nodes: int) -> int:
+    return int(lib().ftle_workspace_bytes(n_nodes))
+
+
+def ftle_advect(mesh: DeviceMesh, flow, t0: float, T: float, dt: float, precision, flowmap, checkpoints=None,
+                ckpt_every: int = 0, options: ftle_options | None = None, stream=None):
+    f = make_flow(flow)
+    _check("ftle_advect", lib().ftle_advect(ctypes.byref(mesh.desc), ctypes.byref(f), t0, T, dt, _prec(precision),
+                                            _ptr(flowmap), _ptr(checkpoints), ckpt_every,
+                                            ctypes.byref(options) if options else None, _stream(stream)))
+
+
+def ftle_gradient_eig(mesh: DeviceMesh, flowmap, precision, T: float, ftle_out, lambda_out, workspace,
+                      options: ftle_options | None = None, stream=None):
+    _check("ftle_gradient_eig",
+           lib().ftle_gradient_eig(ctypes.byref(mesh.desc), _ptr(flowmap), _prec(precision), T, _ptr(ftle_out),
+                                   _ptr(lambda_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                   ctypes.byref(options) if options else None, _stream(stream)))
+
+
+def ftle_refine(mesh: DeviceMesh, flow, t0: float, T: float, dt: float, precision, flowmap, ftle_out, lambda_out,
+                workspace, options: ftle_options | None = None, stream=None):
+    f = make_flow(flow)
+    _check("ftle_refine",
+           lib().ftle_refine(ctypes.byref(mesh.desc), ctypes.byref(f), t0, T, dt, _prec(precision), _ptr(flowmap),
+                             _ptr(ftle_out), _ptr(lambda_out), _ptr(workspace),
+                             workspace.numel() * workspace.element_size(),
+                             ctypes.byref(options) if options else None, _stream(stream)))
+
+
+def ftle_compute(mesh: DeviceMesh, flow, t0: float, T: float, dt: float, precision, flowmap, ftle_out, lambda_out,
+                 workspace, options: ftle_options | None = None, stream=None):
+    f = make_flow(flow)
+    _check("ftle_compute",
+           lib().ftle_compute(ctypes.byref(mesh.desc), ctypes.byref(f), t0, T, dt, _prec(precision), _ptr(flowmap),
+                              _ptr(ftle_out), _ptr(lambda_out), _ptr(workspace),
+                              workspace.numel() * workspace.element_size(),
+                              ctypes.byref(options) if options else None, _stream(stream)))
+
+
+def ftle_host_workspace_bytes(dim: int, n_nodes: int, nnz: int, precision) -> int:
+    return int(lib().ftle_host_workspace_bytes(dim, n_nodes, nnz, _prec(precision)))
+
+
+def ftle_compute_host(coords_host, row_ptr_host, col_idx_host, flow, t0: float, T: float, dt: float, precision,
+                      ftle_host, device_ws, options: ftle_options | None = None, stream=None):
+    """End-to-end call on HOST (preferably pinned) torch tensors; synchronises the stream."""
+    f = make_flow(flow)
+    dim, n = int(coords_host.shape[0]), int(coords_host.shape[1])
+    nnz = int(col_idx_host.numel())
+    _check("ftle_compute_host",
+           lib().ftle_compute_host(dim, n, nnz, _ptr(coords_host), _ptr(row_ptr_host), _ptr(col_idx_host),
+                                   ctypes.byref(f), t0, T, dt, _prec(precision), _ptr(ftle_host), _ptr(device_ws),
+                                   device_ws.numel() * device_ws.element_size(),
+                                   ctypes.byref(options) if options else None, _stream(stream)))
+
+
+def ftle_read_counters(workspace, stream=None) -> dict:
+    c = ftle_counters()
+    _check("ftle_read_counters", lib().ftle_read_counters(_ptr(workspace), ctypes.byref(c), _stream(stream)))
+    return {"n_flagged": int(c.n_flagged), "n_degenerate": int(c.n_degenerate), "n_readvected": int(c.n_readvected)}
+
+
+# ------------------------------------------------------------------------------ buffer helpers
+
+
+def flowmap_empty(dim: int, n_nodes: int, precision, device="cuda"):
+    """Uninitialised flowmap buffer in the layout of ``precision``."""
+    import torch
+
+    p = _prec(precision)
+    if p == PREC["fp64"]:
+        return torch.empty((dim, n_nodes), dtype=torch.float64, device=device)
+    if p == PREC["fp32"]:
+        return torch.empty((dim, n_nodes), dtype=torch.float32, device=device)
+    return torch.empty((dim, n_nodes, 2), dtype=torch.float32, device=device)
+
+
+def workspace_empty(nbytes: int, device="cuda"):
+    """Device byte buffer (torch's allocator returns 256-byte aligned blocks)."""
+    import torch
+
+    t = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    assert t.data_ptr() % 256 == 0
+    return t
+
+
+def ftle_out_empty(n_nodes: int, precision, device="cuda"):
+    import torch
+
+    return torch.empty(n_nodes, dtype=torch.float64 if _prec(precision) == PREC["fp64"] else torch.float32,
+                       device=device)
+
+
+def compute(mesh: DeviceMesh, flow, T: float, dt: float, precision="fp32c", t0: float = 0.0, want_lambda=False,
+            options: ftle_options | None = None, stream=None, return_all=False):
+    """Whole path (advect, gradient/eigen, FP64 refinement) into fresh device tensors."""
+    import torch
+
+    phi = flowmap_empty(mesh.dim, mesh.n_nodes, precision)
+    out = ftle_out_empty(mesh.n_nodes, precision)
+    lam = torch.empty(mesh.n_nodes, dtype=torch.float64, device="cuda") if want_lambda else None
+    ws = workspace_empty(ftle_workspace_bytes(mesh.n_nodes))
+    ftle_compute(mesh, flow, t0, T, dt, precision, phi, out, lam, ws, options, stream)
+    if return_all:
+        return {"ftle": out, "lam": lam, "phi": phi, "workspace": ws}
+    return out

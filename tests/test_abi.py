@@ -1,0 +1,72 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/ftle.h declares
+(no GPU needed: nothing is called that touches a device)."""
+import re
+import subprocess
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def declared_functions():
+    text = (ROOT / "include" / "ftle.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(ftle_[a-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["ftle_advect", "ftle_gradient_eig", "ftle_batch", "ftle_backward", "ftle_compute",
+                 "ftle_status_string", "ftle_workspace_bytes", "ftle_compute_host"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2408_02758_gb300 import ftle
+
+    L = ftle.lib()  # builds with nvcc for sm_103a if stale
+    path = ftle.library_path()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\b(ftle_[a-z0-9_]+)\b", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    assert L.ftle_version() == 1
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2408_02758_gb300 import ftle
+
+    bound = {name for name, _, _ in ftle._SIGS}
+    assert set(declared_functions()) <= bound
+
+
+def test_status_strings_and_host_side_validation():
+    """Argument errors are caught before any device work (no GPU is touched)."""
+    import ctypes
+
+    from paper_2408_02758_gb300 import ftle
+
+    L = ftle.lib()
+    assert L.ftle_status_string(0) == b"ok"
+    assert L.ftle_status_string(-3).startswith(b"workspace")
+    f = ftle.ftle_flow()
+    f.kind = 0
+    m = ftle.ftle_mesh()
+    m.dim = 3  # double gyre is 2D only
+    m.n_nodes = 0
+    rc = L.ftle_advect(ctypes.byref(m), ctypes.byref(f), 0.0, 1.0, 0.01, 2, None, None, 0, None, None)
+    assert rc == ftle.FTLE_EINVAL
+    assert b"2D" in L.ftle_last_error()
+    m.dim = 2
+    rc = L.ftle_advect(ctypes.byref(m), ctypes.byref(f), 0.0, 0.0, 0.01, 2, None, None, 0, None, None)
+    assert rc == ftle.FTLE_EINVAL  # T = 0
+    rc = L.ftle_advect(None, ctypes.byref(f), 0.0, 1.0, 0.01, 2, None, None, 0, None, None)
+    assert rc == ftle.FTLE_EINVAL
+    rc = L.ftle_gradient_eig(ctypes.byref(m), None, 2, 1.0, None, None, None, 0, None, None)
+    assert rc == ftle.FTLE_EWORKSPACE
+    rc = L.ftle_advect(ctypes.byref(m), ctypes.byref(f), 0.0, 1e12, 1e-3, 2, None, None, 0, None, None)
+    assert rc == ftle.FTLE_ERANGE
+    assert L.ftle_flowmap_bytes(2, 10, 2) == 160 and L.ftle_flowmap_bytes(3, 10, 1) == 120
+    assert L.ftle_workspace_bytes(1000) >= 8000

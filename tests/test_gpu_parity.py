@@ -1,0 +1,248 @@
+"""GPU path (libftle.so through its C-ABI) against the FP64 oracle, element by element.
+
+Small cases (the oracle finishes in seconds) span many tiles and a ragged tail; the full-size
+workloads are checked on sampled nodes the oracle computes one by one through a sub-mesh.
+Tolerance (tests/_parity.py): 1e-4 relative where lambda_max > 1 + 1e-3, otherwise
+1e-4 * max|FTLE| absolute; NaN must coincide.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2408_02758_gb300 import inputs as I
+
+from _parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch  # noqa: F401
+
+    from paper_2408_02758_gb300 import ftle
+
+    ftle.lib()
+    return ftle
+
+
+def run_gpu(F, mesh, flow, T, dt, prec, **kw):
+    dm = F.DeviceMesh.from_mesh(mesh)
+    out = F.compute(dm, flow, T, dt, prec, want_lambda=True, return_all=True, **kw)
+    cnt = F.ftle_read_counters(out["workspace"])
+    return out["ftle"].double().cpu().numpy(), out["lam"].cpu().numpy(), out["phi"], cnt
+
+
+def rk4_poly(z):
+    return 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+
+
+# ----------------------------------------------------------------------------- closed forms
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32c"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_saddle_ftle_closed_form(F, prec, dim):
+    if dim == 2:
+        m = I.make_mesh((37, 19), (0, 0), (2, 1), I.TRI, 0.3, 5, coord_dtype=np.float64 if prec == "fp64" else np.float32)
+    else:
+        m = I.make_mesh((9, 7, 6), (0, 0, 0), (1, 1, 1), I.KUHN, 0.25, 6, coord_dtype=np.float64 if prec == "fp64" else np.float32)
+    dt, T = 0.01, 2.0
+    ft, lam, _, cnt = run_gpu(F, m, I.FlowSpec.saddle(), T, dt, prec)
+    expect = math.log(rk4_poly(dt)) / dt
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert np.all(np.abs(ft - expect) <= tol * expect), (np.abs(ft - expect).max(), cnt)
+    assert cnt["n_degenerate"] == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_linear_flow_flowmap_and_ftle(F, prec, dim):
+    rng = np.random.default_rng(20 + dim)
+    M = np.triu(rng.normal(size=(dim, dim))) * 0.5
+    shape = (41, 23) if dim == 2 else (11, 9, 7)
+    m = I.make_mesh(shape, (0,) * dim, (1,) * dim, I.TRI if dim == 2 else I.KUHN, 0.3, 21,
+                    coord_dtype=np.float64 if prec == "fp64" else np.float32)
+    T, dt = 1.5, 0.01
+    ft, lam, phi, _ = run_gpu(F, m, I.FlowSpec.linear(M), T, dt, prec)
+    Z = dt * M
+    P = np.eye(dim) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+    P = np.linalg.matrix_power(P, 150)
+    x0 = m.coords.astype(np.float64)
+    ph = phi.double().cpu().numpy()
+    if prec == "fp32c":
+        ph = ph[..., 0] + ph[..., 1]
+    assert np.abs(ph - P @ x0).max() < (1e-12 if prec == "fp64" else 1e-6)
+    smax = np.linalg.svd(P, compute_uv=False)[0]
+    expect = math.log(smax) / T
+    assert np.abs(ft - expect).max() <= (1e-10 if prec == "fp64" else 1e-5) * abs(expect)
+
+
+# ----------------------------------------------------------------------------- oracle parity
+
+
+def _oracle_full(mesh, flow, T, dt):
+    return O.ftle(flow.kind, flow.params, mesh.coords, mesh.row_ptr, mesh.col_idx, T, dt)
+
+
+def test_structured_double_gyre_fp64_full_size(F):
+    """256 x 128 structured grid, 4-neighbour stencil, T = 10, everything in double."""
+    w = I.preset(0)
+    ft, lam, _, cnt = run_gpu(F, w.mesh, w.flow, w.T, w.dt, "fp64")
+    o = _oracle_full(w.mesh, w.flow, w.T, w.dt)
+    rep = compare(ft, o["ftle"], o["lam"], rel_tol=1e-9)
+    assert rep["ok"], rep
+    assert cnt["n_degenerate"] == 0
+
+
+@pytest.mark.parametrize("scale", [1 / 16, 3 / 64])
+def test_triangle_double_gyre_fp32c_small(F, scale):
+    """Jittered triangle mesh (128 x 64 and a ragged 96 x 48), double gyre T = 15, fp32c + FP64 path."""
+    w = I.preset(1, scale=scale)
+    ft, lam, _, cnt = run_gpu(F, w.mesh, w.flow, w.T, w.dt, "fp32c")
+    o = _oracle_full(w.mesh, w.flow, w.T, w.dt)
+    rep = compare(ft, o["ftle"], o["lam"])
+    print(rep, cnt)
+    assert rep["ok"], (rep, cnt)
+
+
+def test_abc_kuhn_fp32c_small(F):
+    """32^3 jittered Kuhn tetrahedral mesh (14 neighbours), ABC flow, T = 5."""
+    w = I.preset(2, scale=1 / 8)
+    ft, lam, _, cnt = run_gpu(F, w.mesh, w.flow, w.T, w.dt, "fp32c")
+    o = _oracle_full(w.mesh, w.flow, w.T, w.dt)
+    rep = compare(ft, o["ftle"], o["lam"])
+    print(rep, cnt)
+    assert rep["ok"], (rep, cnt)
+
+
+def test_flowmap_parity_fp32c(F):
+    w = I.preset(1, scale=1 / 32)
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    phi = F.flowmap_empty(2, w.mesh.n_nodes, "fp32c")
+    F.ftle_advect(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi)
+    ph = phi.double().cpu().numpy()
+    ph = ph[..., 0] + ph[..., 1]
+    ref = O.advect(w.flow.kind, w.flow.params, w.mesh.coords, w.T, w.dt)
+    err = np.abs(ph - ref)
+    # separatrix nodes amplify rounding by up to ~1e4; the bulk stays near float's resolution
+    assert np.median(err) < 1e-6 and err.max() < 5e-3
+
+
+@pytest.mark.parametrize("idx,n_sample", [(1, 3000), (2, 600)])
+def test_full_size_workload_sampled(F, idx, n_sample):
+    """The benchmark's workloads at full size (2.1M-node triangle mesh; 16.7M-node tet mesh), in the
+    same launch configuration the benchmark times; the oracle evaluates sampled nodes."""
+    w = I.preset(idx)
+    ft, lam, _, cnt = run_gpu(F, w.mesh, w.flow, w.T, w.dt, w.precision)
+    rng = np.random.default_rng(100 + idx)
+    rows = np.sort(rng.choice(w.mesh.n_nodes, n_sample, replace=False))
+    # always include the first and last nodes (corners) and a boundary row
+    rows = np.unique(np.concatenate([rows, [0, w.mesh.n_nodes - 1, w.mesh.shape[0] // 2]]))
+    o = O.ftle_sample(w.flow.kind, w.flow.params, w.mesh.coords, w.mesh.row_ptr, w.mesh.col_idx, rows, w.T, w.dt)
+    rep = compare(ft[rows], o["ftle"], o["lam"])
+    print(rep, cnt)
+    assert rep["ok"], (rep, cnt)
+    assert np.isfinite(ft).all()
+    assert cnt["n_degenerate"] == 0
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+
+def test_degenerate_rows_give_nan_and_are_counted(F):
+    import torch
+
+    # node 0: collinear neighbours; node 1: one neighbour; node 2: none; node 3: fine; node 4: none
+    x = np.array([[0.0, 1.0, 2.0, 0.0, 1.0], [0.0, 0.0, 0.0, 1.0, 1.0]], dtype=np.float32)
+    rp = np.array([0, 2, 3, 3, 6, 6], dtype=np.int32)
+    ci = np.array([1, 2, 0, 0, 1, 4], dtype=np.int32)
+    mesh = I.mesh_from_arrays(x, rp, ci)
+    for prec in ("fp64", "fp32", "fp32c"):
+        m2 = I.mesh_from_arrays(x.astype(np.float64) if prec == "fp64" else x, rp, ci)
+        ft, lam, _, cnt = run_gpu(F, m2, I.FlowSpec.linear(np.array([[1.0, 0.0], [0.0, 1.0]])), 0.5, 0.01, prec)
+        assert np.isnan(ft[[0, 1, 2, 4]]).all(), (prec, ft)
+        assert cnt["n_degenerate"] == 4, (prec, cnt)
+        expect = math.log(rk4_poly(0.01)) / 0.01
+        assert abs(ft[3] - expect) < 1e-5
+    del mesh, torch
+
+
+def test_empty_mesh_is_a_no_op(F):
+    import torch
+
+    m = I.mesh_from_arrays(np.zeros((2, 0), np.float32), np.zeros(1, np.int32), np.zeros(0, np.int32))
+    dm = F.DeviceMesh(torch.zeros((2, 0), device="cuda"), torch.zeros(1, dtype=torch.int32, device="cuda"),
+                      torch.zeros(1, dtype=torch.int32, device="cuda"))
+    dm.desc.nnz = 0
+    out = F.compute(dm, I.FlowSpec.saddle(), 1.0, 0.01, "fp32c")
+    assert out.numel() == 0
+    del m
+
+
+def test_single_node_and_ragged_tail(F):
+    # 257 x 3 lattice: n = 771, not a multiple of the block size
+    m = I.make_mesh((257, 3), (0, 0), (2, 1), I.TRI, 0.3, 31)
+    ft, lam, _, cnt = run_gpu(F, m, I.FlowSpec.double_gyre(), 3.0, 0.01, "fp32c")
+    o = _oracle_full(m, I.FlowSpec.double_gyre(), 3.0, 0.01)
+    rep = compare(ft, o["ftle"], o["lam"])
+    assert rep["ok"], rep
+    one = I.mesh_from_arrays(np.zeros((2, 1), np.float32), np.zeros(2, np.int32), np.zeros(0, np.int32))
+    import torch
+
+    dm = F.DeviceMesh(torch.zeros((2, 1), device="cuda"), torch.zeros(2, dtype=torch.int32, device="cuda"),
+                      torch.zeros(1, dtype=torch.int32, device="cuda"))
+    dm.desc.nnz = 0
+    out = F.compute(dm, I.FlowSpec.saddle(), 1.0, 0.01, "fp32c")
+    assert torch.isnan(out).all()
+    del one
+
+
+def test_backward_time_horizon(F):
+    w = I.preset(1, scale=1 / 32)
+    ft, lam, _, cnt = run_gpu(F, w.mesh, w.flow, -5.0, w.dt, "fp32c")
+    o = _oracle_full(w.mesh, w.flow, -5.0, w.dt)
+    rep = compare(ft, o["ftle"], o["lam"])
+    assert rep["ok"], rep
+
+
+def test_deterministic(F):
+    w = I.preset(2, scale=1 / 16)
+    a = run_gpu(F, w.mesh, w.flow, 2.0, w.dt, "fp32c")[0]
+    b = run_gpu(F, w.mesh, w.flow, 2.0, w.dt, "fp32c")[0]
+    assert np.array_equal(a, b)
+
+
+def test_host_entry_point_matches_device_entry_point(F):
+    import torch
+
+    w = I.preset(1, scale=1 / 16)
+    dev = run_gpu(F, w.mesh, w.flow, w.T, w.dt, "fp32c")[0]
+    ch = torch.from_numpy(w.mesh.coords).pin_memory()
+    rp = torch.from_numpy(w.mesh.row_ptr).pin_memory()
+    ci = torch.from_numpy(w.mesh.col_idx).pin_memory()
+    out = torch.empty(w.mesh.n_nodes, dtype=torch.float32).pin_memory()
+    ws = F.workspace_empty(F.ftle_host_workspace_bytes(2, w.mesh.n_nodes, w.mesh.nnz, "fp32c"))
+    F.ftle_compute_host(ch, rp, ci, w.flow, 0.0, w.T, w.dt, "fp32c", out, ws)
+    assert np.array_equal(out.double().numpy(), dev)
+
+
+def test_invalid_arguments_raise(F):
+    import torch
+
+    w = I.preset(1, scale=1 / 64)
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    phi = F.flowmap_empty(2, w.mesh.n_nodes, "fp32c")
+    out = F.ftle_out_empty(w.mesh.n_nodes, "fp32c")
+    small = F.workspace_empty(256)
+    with pytest.raises(F.FTLEError) as e:
+        F.ftle_gradient_eig(dm, phi, "fp32c", 1.0, out, None, small)
+    assert e.value.status == F.FTLE_EWORKSPACE
+    with pytest.raises(F.FTLEError) as e:
+        F.ftle_advect(dm, I.FlowSpec.abc(), 0.0, 1.0, 0.01, "fp32c", phi)
+    assert e.value.status == F.FTLE_EINVAL
+    with pytest.raises(F.FTLEError):
+        F.ftle_advect(dm, w.flow, 0.0, 1.0, 0.0, "fp32c", phi)
+    torch.cuda.synchronize()
