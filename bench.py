@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--workload", type=int, default=1, help="preset index (0..2; 1 is the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="lattice axes scaled by this factor (smaller cases for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -192,7 +194,7 @@ def main():
     world, rank, local = dist_setup()
     from paper_2408_02758_gb300 import inputs as I
 
-    w = I.preset(args.workload)
+    w = I.preset(args.workload, scale=args.scale)
 
     if args.impl == "reference":
         run_reference(args, w, world, rank)

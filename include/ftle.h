@@ -111,7 +111,9 @@ typedef struct ftle_options {
   int32_t advect_blocks_per_sm; /* resident blocks per SM the advection grid is sized for */
   int32_t grad_block;     /* threads per block of the gradient kernel (multiple of 32) */
   int32_t grad_tile;      /* nodes per gradient tile (multiple of grad_block) */
-  int32_t reserved[4];
+  int32_t refine_lanes;   /* FP64 re-advection: active lanes per 32-thread block (1..32); fewer
+                             lanes spread the few flagged nodes over more SM sub-partitions */
+  int32_t reserved[3];
 } ftle_options;
 
 /* ---------------------------------------------------------------------------------- sizes */

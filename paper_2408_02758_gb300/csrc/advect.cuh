@@ -27,6 +27,7 @@ struct AdvArgs {
   double p[12];                // flow parameters
   const int32_t* list;         // nullable: process list[0 .. *list_count)
   const unsigned long long* list_count;
+  int lanes;                   // active threads per block (0 = all): few-node lists spread wider
 };
 
 // ------------------------------------------------------------------------- velocity dispatch
@@ -146,10 +147,10 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
   const double nu = a.p[2] / kPi;  // omega / pi (double gyre)
   bool table_valid = false;        // single-chunk tables are built once per block
 
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count;
-       base += (int64_t)gridDim.x * blockDim.x) {
+  const int lanes = (a.lanes > 0 && a.lanes < (int)blockDim.x) ? a.lanes : (int)blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * lanes; base < count; base += (int64_t)gridDim.x * lanes) {
     const int64_t slot = base + threadIdx.x;
-    const bool active = slot < count;
+    const bool active = (int)threadIdx.x < lanes && slot < count;
     const int64_t i = active ? (a.list ? (int64_t)a.list[slot] : slot) : 0;
 
     float xh[DIM], xl[DIM];

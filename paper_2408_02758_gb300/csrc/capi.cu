@@ -134,6 +134,7 @@ Launch resolve_launch(const ftle_options* opt) {
     if (opt->advect_block > 0) L.advect_block = opt->advect_block;
     if (opt->advect_blocks_per_sm > 0) L.advect_bps = opt->advect_blocks_per_sm;
     if (opt->grad_block > 0) L.grad_block = opt->grad_block;
+    if (opt->refine_lanes > 0) L.refine_lanes = opt->refine_lanes;
   }
   return L;
 }
@@ -144,6 +145,7 @@ int check_launch(const Launch& L) {
   if (L.grad_block % 32 || L.grad_block < 32 || L.grad_block > 256)
     return fail(FTLE_EINVAL, "grad_block must be a multiple of 32 in [32, 256]");
   if (L.advect_bps < 1 || L.advect_bps > 64) return fail(FTLE_EINVAL, "advect_blocks_per_sm in [1, 64]");
+  if (L.refine_lanes < 1 || L.refine_lanes > 32) return fail(FTLE_EINVAL, "refine_lanes in [1, 32]");
   return FTLE_OK;
 }
 
@@ -252,7 +254,8 @@ int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
   a.out = phi;
   a.list = mark;
   a.list_count = &hdr->n_readvected;
-  rc = launch_advect(fl->kind, m->dim, P64, O32PAIR, m->coord_fp64 != 0, a, sms * 2, 64, s);
+  a.lanes = L.refine_lanes;
+  rc = launch_advect(fl->kind, m->dim, P64, O32PAIR, m->coord_fp64 != 0, a, sms * 4, 32, s);
   if (rc) return rc;
   return launch_grad_f64(m->dim, PHI32PAIR, m->coord_fp64 != 0, false, g, sms * 4, 128, s);
 }

@@ -12,6 +12,7 @@ struct Launch {
   int advect_block = 256;
   int advect_bps = 8;     // resident blocks per SM for 256-thread blocks (scaled for others)
   int grad_block = 256;
+  int refine_lanes = 32;
 };
 
 int check_mesh(const ftle_mesh* m);

@@ -52,7 +52,7 @@ def test_saddle_ftle_closed_form(F, prec, dim):
     dt, T = 0.01, 2.0
     ft, lam, _, cnt = run_gpu(F, m, I.FlowSpec.saddle(), T, dt, prec)
     expect = math.log(rk4_poly(dt)) / dt
-    tol = 1e-12 if prec == "fp64" else 2e-6
+    tol = {"fp64": 1e-12, "fp32c": 2e-6, "fp32": 1e-4}[prec]  # plain fp32 rounds the state every step
     assert np.all(np.abs(ft - expect) <= tol * expect), (np.abs(ft - expect).max(), cnt)
     assert cnt["n_degenerate"] == 0
 
