@@ -183,6 +183,30 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
 /* Synchronous read of the counters at the start of `workspace` (waits for `stream`). */
 int ftle_read_counters(const void* workspace, ftle_counters* out, void* stream);
 
+/* FTLE core with no device allocation anywhere, for callers that may not allocate.  The paper
+ * has no counterpart; this is a service of the library.  Some callers cannot hand the library a
+ * workspace: a plugin whose host application owns every device allocation, a component that runs
+ * under a fixed device-memory budget fixed at start-up, or a latency-critical loop that must not
+ * call cudaMalloc / cudaFree (cudaFree can synchronise the whole device).  This entry point does
+ * the work of ftle_gradient_eig with its scratch (the counters and the list of nodes that take
+ * the FP64 path) in a file-scope device array of the library instead of a caller workspace.
+ *   - Limit: n_nodes <= FTLE_NOALLOC_MAX_NODES; larger meshes return FTLE_ERANGE, nothing launched.
+ *   - Memory: the array (FTLE_NOALLOC_MAX_NODES * 4 + 256 bytes, about 4 MiB) is part of the
+ *     library's device image, so every GPU that loads libftle.so holds it until the process exits.
+ *   - Set-up: the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ *     capture begins on the device.
+ *   - Sharing: all calls share the one array, and each call clears the counters it needs at its
+ *     start (the array keeps the last call's contents otherwise).  Two calls whose work overlaps
+ *     on the GPU (for example on two streams) race on the array and corrupt each other's FP64
+ *     node list; serialise them.
+ *   - Arguments, outputs and errors otherwise as ftle_gradient_eig (flowmap, ftle_out and
+ *     lambda_out are caller device buffers; no counters are returned). */
+#define FTLE_NOALLOC_MAX_NODES 1048576
+int ftle_gradient_eig_noalloc(const ftle_mesh* mesh, const void* flowmap, int32_t precision, double T,
+                              void* ftle_out, double* lambda_out, const ftle_options* opt,
+                              void* stream);
+
 /* ---------------------------------------------------------------------------------- batched */
 
 /* Many independent problems of uneven size and horizon in one launch sequence: one persistent

@@ -72,6 +72,8 @@ _SIGS = [
                                   c_double, c_double, c_double, c_int32, c_void_p, c_void_p, c_size_t,
                                   POINTER(ftle_options), c_void_p]),
     ("ftle_read_counters", c_int, [c_void_p, POINTER(ftle_counters), c_void_p]),
+    ("ftle_gradient_eig_noalloc", c_int, [POINTER(ftle_mesh), c_void_p, c_int32, c_double, c_void_p, c_void_p,
+                                          POINTER(ftle_options), c_void_p]),
     ("ftle_batch_workspace_bytes", c_size_t, [c_int32, POINTER(ftle_mesh), c_int32]),
     ("ftle_batch", c_int, [c_int32, POINTER(ftle_mesh), POINTER(ftle_flow), POINTER(c_double), c_double, c_int32,
                            POINTER(c_void_p), c_void_p, c_size_t, POINTER(ftle_options), c_void_p]),
@@ -223,6 +225,19 @@ def ftle_gradient_eig(mesh: DeviceMesh, flowmap, precision, T: float, ftle_out, 
            lib().ftle_gradient_eig(ctypes.byref(mesh.desc), _ptr(flowmap), _prec(precision), T, _ptr(ftle_out),
                                    _ptr(lambda_out), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                    ctypes.byref(options) if options else None, _stream(stream)))
+
+
+NOALLOC_MAX_NODES = 1048576
+
+
+def ftle_gradient_eig_noalloc(mesh: DeviceMesh, flowmap, precision, T: float, ftle_out, lambda_out,
+                              options: ftle_options | None = None, stream=None):
+    """FTLE core without a workspace: the scratch lives in a static device array of the library
+    (at most NOALLOC_MAX_NODES nodes; calls that overlap on the GPU race on it)."""
+    _check("ftle_gradient_eig_noalloc",
+           lib().ftle_gradient_eig_noalloc(ctypes.byref(mesh.desc), _ptr(flowmap), _prec(precision), T,
+                                           _ptr(ftle_out), _ptr(lambda_out),
+                                           ctypes.byref(options) if options else None, _stream(stream)))
 
 
 def ftle_refine(mesh: DeviceMesh, flow, t0: float, T: float, dt: float, precision, flowmap, ftle_out, lambda_out,
