@@ -74,7 +74,7 @@ typedef enum ftle_flow_kind {
  *   FP32C: float RK4 stages with a compensated (two-sum) state and velocity evaluated at the
  *          compensated stage point; the flowmap is stored as (hi, lo) float pairs,
  *          flowmap: float2 [dim][n] (hi at even, lo at odd float index); gradient in float,
- *          with the FP64 path for the nodes where float cancels (see ftle_options.refine_mu).
+ *          with the FP64 path for the nodes where float cancels (see ftle_options.refine_kappa).
  *          ftle_out: float [n]. */
 typedef enum ftle_precision { FTLE_PREC_FP64 = 0, FTLE_PREC_FP32 = 1, FTLE_PREC_FP32C = 2 } ftle_precision;
 
@@ -104,15 +104,18 @@ typedef struct ftle_counters {
 
 /* Optional tuning; pass NULL for defaults.  Zero fields mean "default". */
 typedef struct ftle_options {
-  double refine_mu;       /* FP32/FP32C: nodes with lambda_max - 1 < refine_mu take the FP64
-                             path (default 0.1 when the field is 0; negative turns this test off,
-                             rank and conditioning checks still send nodes to FP64) */
+  double refine_kappa;    /* FP32/FP32C: node i takes the FP64 gradient (and, in ftle_refine,
+                             the float-float re-advection) when ln(lambda_max) * h_i < refine_kappa,
+                             h_i its RMS neighbour distance: the float flowmap's error relative to
+                             h_i, divided by ln(lambda_max), bounds the FTLE's relative error.
+                             Default 4e-4 when the field is 0; negative turns this test off (the
+                             rank, conditioning and lambda_max - 1 < 0.01 checks remain). */
   int32_t advect_block;   /* threads per block of the advection kernel (multiple of 32) */
   int32_t advect_blocks_per_sm; /* resident blocks per SM the advection grid is sized for */
   int32_t grad_block;     /* threads per block of the gradient kernel (multiple of 32) */
   int32_t grad_tile;      /* nodes per gradient tile (multiple of grad_block) */
-  int32_t refine_lanes;   /* FP64 re-advection: active lanes per 32-thread block (1..32); fewer
-                             lanes spread the few flagged nodes over more SM sub-partitions */
+  int32_t refine_lanes;   /* re-advection: active lanes per 32-thread block (1..32); fewer lanes
+                             spread a short node list over more SM sub-partitions */
   int32_t reserved[3];
 } ftle_options;
 
@@ -154,9 +157,10 @@ int ftle_gradient_eig(const ftle_mesh* mesh, const void* flowmap, int32_t precis
                       void* ftle_out, double* lambda_out, void* workspace, size_t workspace_bytes,
                       const ftle_options* opt, void* stream);
 
-/* FP32C only (no-op for other precisions): re-advects in FP64 the nodes listed by the last
- * ftle_gradient_eig on this workspace together with their neighbours, writes their flowmap
- * back as exact (hi, lo) pairs, and recomputes the listed nodes' FTLE in FP64.  Must follow
+/* FP32C only (no-op for other precisions): re-advects in float-float arithmetic (~48 bits, on
+ * the FP32 pipes) the nodes listed by the last ftle_gradient_eig on this workspace together
+ * with their neighbours, writes their flowmap back as (hi, lo) pairs, and recomputes the listed
+ * nodes' FTLE in FP64.  Must follow
  * ftle_gradient_eig on the same stream, mesh, flowmap and workspace. */
 int ftle_refine(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double T, double dt,
                 int32_t precision, void* flowmap, void* ftle_out, double* lambda_out,

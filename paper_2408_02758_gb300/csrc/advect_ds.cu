@@ -1,0 +1,152 @@
+// Float-float RK4 re-advection of a short node list (the nodes the float gradient kernel flagged
+// and their neighbours).  Same scheme and stage times as k_advect, every operation in
+// float-float (~48-bit) arithmetic on the FP32 pipes; one node per lane, 32-thread blocks so the
+// few warps spread over the SM sub-partitions.  The double-gyre coefficient a(t) is tabulated
+// per block in double and split into float-float.
+#include "advect.cuh"
+#include "capi_internal.cuh"
+#include "dsfloat.cuh"
+
+namespace ftle {
+
+struct DsFlow {
+  dsf c[9];
+};
+
+template <int KIND, int DIM>
+__device__ __forceinline__ void vel_ds(const DsFlow& F, const dsf* x, dsf a, dsf* u) {
+  if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE) {
+    const dsf b = ds_add_f(ds_make(-2.0f * a.h, -2.0f * a.l), 1.0f);  // b = 1 - 2a
+    const dsf t1 = ds_mul(a, x[0]);
+    const dsf f = ds_mul(ds_add(t1, b), x[0]);                        // a x^2 + b x
+    const dsf fx = ds_add(ds_make(2.0f * t1.h, 2.0f * t1.l), b);      // 2 a x + b
+    dsf sf, cf, sy, cy;
+    ds_sincospi(f, sf, cf);
+    ds_sincospi(x[1], sy, cy);
+    u[0] = ds_neg(ds_mul(ds_mul(F.c[0], sf), cy));
+    u[1] = ds_mul(ds_mul(ds_mul(F.c[0], cf), sy), fx);
+  } else if constexpr (KIND == FTLE_FLOW_ABC) {
+    dsf sx, cx, sy, cy, sz, cz;
+    ds_sincos(x[0], sx, cx);
+    ds_sincos(x[1], sy, cy);
+    ds_sincos(x[2], sz, cz);
+    u[0] = ds_add(ds_mul(F.c[0], sz), ds_mul(F.c[2], cy));
+    u[1] = ds_add(ds_mul(F.c[1], sx), ds_mul(F.c[0], cz));
+    u[2] = ds_add(ds_mul(F.c[2], sy), ds_mul(F.c[1], cx));
+  } else if constexpr (KIND == FTLE_FLOW_LINEAR) {
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      dsf s = ds_mul(F.c[r * DIM], x[0]);
+#pragma unroll
+      for (int c = 1; c < DIM; ++c) s = ds_add(s, ds_mul(F.c[r * DIM + c], x[c]));
+      u[r] = s;
+    }
+  } else {
+    u[0] = x[0];
+    u[1] = ds_neg(x[1]);
+    if constexpr (DIM == 3) u[2] = ds_make(0.f, 0.f);
+  }
+}
+
+template <int DIM>
+__device__ __forceinline__ void ds_axpy(const dsf* x, dsf h, const dsf* k, dsf* y) {
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) y[d] = ds_add(x[d], ds_mul(h, k[d]));
+}
+
+template <int KIND, int DIM, typename CT>
+__global__ void __launch_bounds__(32) k_advect_ds(AdvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dsf* tab = reinterpret_cast<dsf*>(smem_raw);
+  constexpr bool kTable = (KIND == FTLE_FLOW_DOUBLE_GYRE);
+
+  const int64_t count = a.list ? (int64_t)*a.list_count : a.n;
+  const int nchunks = (a.nsteps + kAdvChunk - 1) / kAdvChunk;
+  DsFlow F;
+  if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE) {
+    F.c[0] = ds_from_double(kPi * a.p[0]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) F.c[q] = ds_from_double(a.p[q]);
+  }
+  const dsf h = ds_from_double(a.h), h2 = ds_from_double(0.5 * a.h), h6 = ds_from_double(a.h / 6.0);
+  bool table_valid = false;
+
+  const int lanes = (a.lanes > 0 && a.lanes < (int)blockDim.x) ? a.lanes : (int)blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * lanes; base < count; base += (int64_t)gridDim.x * lanes) {
+    const int64_t slot = base + threadIdx.x;
+    const bool active = (int)threadIdx.x < lanes && slot < count;
+    const int64_t i = active ? (a.list ? (int64_t)a.list[slot] : slot) : 0;
+    dsf x[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+      x[d] = ds_from_double(active ? (double)__ldg(reinterpret_cast<const CT*>(a.coords) + d * a.n_mesh + i) : 0.0);
+
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int k0 = ch * kAdvChunk;
+      const int k1 = min(a.nsteps, k0 + kAdvChunk);
+      if constexpr (kTable) {
+        if (!(table_valid && nchunks == 1)) {
+          __syncthreads();
+          for (int m = threadIdx.x; m <= 2 * (k1 - k0); m += blockDim.x)
+            tab[m] = ds_from_double(a.p[1] * sin(a.p[2] * (a.t0 + 0.5 * a.h * (double)(2 * k0 + m))));
+          __syncthreads();
+          table_valid = true;
+        }
+      }
+      if (!active) continue;
+      for (int k = k0; k < k1; ++k) {
+        const int m = 2 * (k - k0);
+        dsf c0 = ds_make(0.f, 0.f), c1 = c0, c2 = c0;
+        if constexpr (kTable) {
+          c0 = tab[m];
+          c1 = tab[m + 1];
+          c2 = tab[m + 2];
+        }
+        dsf k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], y[DIM];
+        vel_ds<KIND, DIM>(F, x, c0, k1v);
+        ds_axpy<DIM>(x, h2, k1v, y);
+        vel_ds<KIND, DIM>(F, y, c1, k2v);
+        ds_axpy<DIM>(x, h2, k2v, y);
+        vel_ds<KIND, DIM>(F, y, c1, k3v);
+        ds_axpy<DIM>(x, h, k3v, y);
+        vel_ds<KIND, DIM>(F, y, c2, k4v);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          const dsf s23 = ds_add(k2v[d], k3v[d]);
+          const dsf s = ds_add(ds_add(k1v[d], k4v[d]), ds_make(2.0f * s23.h, 2.0f * s23.l));
+          x[d] = ds_add(x[d], ds_mul(h6, s));
+        }
+      }
+    }
+    if (active) {
+      float2* o = reinterpret_cast<float2*>(a.out);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) o[d * a.n_mesh + i] = make_float2(x[d].h, x[d].l);
+    }
+  }
+}
+
+template <int KIND, int DIM>
+static void ds_dispatch(bool coord64, const AdvArgs& args, int grid, int block, size_t smem, cudaStream_t s) {
+  if (coord64)
+    k_advect_ds<KIND, DIM, double><<<grid, block, smem, s>>>(args);
+  else
+    k_advect_ds<KIND, DIM, float><<<grid, block, smem, s>>>(args);
+}
+
+int launch_advect_ds(int kind, int dim, bool coord64, const AdvArgs& args, int grid, int block,
+                     cudaStream_t stream) {
+  const size_t smem = advect_smem_bytes(kind, P32, args.nsteps);  // one float pair per half step
+  if (kind == FTLE_FLOW_DOUBLE_GYRE && dim == 2) ds_dispatch<FTLE_FLOW_DOUBLE_GYRE, 2>(coord64, args, grid, block, smem, stream);
+  else if (kind == FTLE_FLOW_ABC && dim == 3) ds_dispatch<FTLE_FLOW_ABC, 3>(coord64, args, grid, block, smem, stream);
+  else if (kind == FTLE_FLOW_LINEAR && dim == 2) ds_dispatch<FTLE_FLOW_LINEAR, 2>(coord64, args, grid, block, smem, stream);
+  else if (kind == FTLE_FLOW_LINEAR && dim == 3) ds_dispatch<FTLE_FLOW_LINEAR, 3>(coord64, args, grid, block, smem, stream);
+  else if (kind == FTLE_FLOW_SADDLE && dim == 2) ds_dispatch<FTLE_FLOW_SADDLE, 2>(coord64, args, grid, block, smem, stream);
+  else if (kind == FTLE_FLOW_SADDLE && dim == 3) ds_dispatch<FTLE_FLOW_SADDLE, 3>(coord64, args, grid, block, smem, stream);
+  else return fail(FTLE_EUNSUPPORTED, "float-float advection: flow %d in %dD", kind, dim);
+  FTLE_LAUNCH_CHECK("k_advect_ds launch");
+  return FTLE_OK;
+}
+
+}  // namespace ftle

@@ -130,7 +130,7 @@ int check_workspace(const void* ws, size_t bytes, size_t need) {
 Launch resolve_launch(const ftle_options* opt) {
   Launch L;
   if (opt) {
-    if (opt->refine_mu != 0.0) L.refine_mu = opt->refine_mu;
+    if (opt->refine_kappa != 0.0) L.refine_kappa = opt->refine_kappa;
     if (opt->advect_block > 0) L.advect_block = opt->advect_block;
     if (opt->advect_blocks_per_sm > 0) L.advect_bps = opt->advect_blocks_per_sm;
     if (opt->grad_block > 0) L.grad_block = opt->grad_block;
@@ -203,7 +203,7 @@ GradArgs make_grad_args(const ftle_mesh* m, const void* phi, double T, void* ftl
   g.ftle_out = ftle_out;
   g.lam_out = lam_out;
   g.inv_2absT = 1.0 / (2.0 * fabs(T));
-  g.refine_mu = (float)L.refine_mu;
+  g.refine_kappa = (float)L.refine_kappa;
   g.hdr = reinterpret_cast<ftle_counters*>(w + W.header);
   g.flag_list = reinterpret_cast<int32_t*>(w + W.flag_list);
   return g;
@@ -236,7 +236,7 @@ int run_gradient(const ftle_mesh* m, const void* phi, int precision, double T, v
 int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, double dt, int nsteps,
                int precision, void* phi, void* ftle_out, double* lam_out, void* ws, const Launch& L,
                cudaStream_t s) {
-  if (precision != FTLE_PREC_FP32C || m->n_nodes == 0 || L.refine_mu < 0) return FTLE_OK;
+  if (precision != FTLE_PREC_FP32C || m->n_nodes == 0 || L.refine_kappa < 0) return FTLE_OK;
   const WsLayout W = ws_layout(m->n_nodes);
   char* w = reinterpret_cast<char*>(ws);
   ftle_counters* hdr = reinterpret_cast<ftle_counters*>(w + W.header);
@@ -255,7 +255,7 @@ int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
   a.list = mark;
   a.list_count = &hdr->n_readvected;
   a.lanes = L.refine_lanes;
-  rc = launch_advect(fl->kind, m->dim, P64, O32PAIR, m->coord_fp64 != 0, a, sms * 4, 32, s);
+  rc = launch_advect_ds(fl->kind, m->dim, m->coord_fp64 != 0, a, sms * 8, 32, s);
   if (rc) return rc;
   return launch_grad_f64(m->dim, PHI32PAIR, m->coord_fp64 != 0, false, g, sms * 4, 128, s);
 }

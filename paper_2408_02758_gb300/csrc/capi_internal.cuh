@@ -8,7 +8,7 @@
 namespace ftle {
 
 struct Launch {
-  double refine_mu = 0.1;
+  double refine_kappa = 4e-4;
   int advect_block = 256;
   int advect_bps = 8;     // resident blocks per SM for 256-thread blocks (scaled for others)
   int grad_block = 256;
@@ -29,6 +29,8 @@ int launch_advect_dg(int prec, int out, bool coord64, const AdvArgs& args, int g
                      size_t smem, cudaStream_t stream);
 int launch_advect_abc(int prec, int out, bool coord64, const AdvArgs& args, int grid, int block,
                       size_t smem, cudaStream_t stream);
+int launch_advect_ds(int kind, int dim, bool coord64, const AdvArgs& args, int grid, int block,
+                     cudaStream_t stream);
 int launch_advect_misc(int kind, int dim, int prec, int out, bool coord64, const AdvArgs& args,
                        int grid, int block, size_t smem, cudaStream_t stream);
 

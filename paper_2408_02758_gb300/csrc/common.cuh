@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "ftle.h"
+#include "poly_coef.cuh"
 
 namespace ftle {
 
@@ -50,6 +51,62 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Dekker's Fast2Sum: s + e == a + b exactly when |a| >= |b| (or a == 0).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// ------------------------------------------------------------------------ float sin / cos
+
+constexpr float kRoundMagic = 12582912.0f;  // 1.5 * 2^23: x + magic rounds x to an integer
+
+// (sin, cos) of q quarter turns plus the reduced argument, from the reduced pair (sr, cr); q is
+// the integer held in the low bits of the magic-rounded float t.
+__device__ __forceinline__ void quarter_turn(float t, float sr, float cr, float& s, float& c) {
+  const int q = __float_as_int(t);
+  const bool odd = q & 1;
+  const float a = odd ? cr : sr, b = odd ? sr : cr;
+  s = __int_as_float(__float_as_int(a) ^ ((q << 30) & 0x80000000));
+  c = __int_as_float(__float_as_int(b) ^ (((q + 1) << 30) & 0x80000000));
+}
+
+// sin(pi x), cos(pi x): x = k/2 + r with k = rint(2x) and r = x - k/2 exact, |r| <= 1/4;
+// minimax polynomials (gen_poly.py) on r, then k quarter turns.  Valid for |x| < 2^21.
+__device__ __forceinline__ void fsincospi(float x, float& s, float& c) {
+  const float t = fmaf(x, 2.0f, kRoundMagic);
+  const float k = __fsub_rn(t, kRoundMagic);
+  const float r = fmaf(k, -0.5f, x);
+  const float z = r * r;
+  const float ps = fmaf(fmaf(fmaf(kPI_S[3], z, kPI_S[2]), z, kPI_S[1]), z, kPI_S[0]) * r;
+  const float pc = fmaf(fmaf(fmaf(fmaf(kPI_C[4], z, kPI_C[3]), z, kPI_C[2]), z, kPI_C[1]), z, kPI_C[0]);
+  quarter_turn(t, ps, pc, s, c);
+}
+
+// pi/2 in three parts: A (8 significant bits) and B (13) make k*A and k*B exact for |k| < 2^11;
+// C is the rest, rounded.
+constexpr float kPio2A = 0x1.92p+0f;
+constexpr float kPio2B = 0x1.fb4p-12f;
+constexpr float kPio2C = (float)(1.57079632679489661923 - (double)0x1.92p+0 - (double)0x1.fb4p-12);
+
+// sin(x), cos(x) at the compensated point xh + xl: x = k pi/2 + r, r carried as rh + rl (the
+// reduction residual and xl go to rl), minimax polynomials on rh, and the first-order
+// correction rl * (cos, -sin).  Valid for |x| < 2^11 * pi/2.
+__device__ __forceinline__ void fsincos_c(float xh, float xl, float& s, float& c) {
+  const float t = fmaf(xh, 0.636619772367581343f, kRoundMagic);
+  const float k = __fsub_rn(t, kRoundMagic);
+  const float r1 = fmaf(-k, kPio2A, xh);  // exact (Sterbenz; k * A exact)
+  float rh, re;
+  two_sum(r1, -k * kPio2B, rh, re);  // -k * B exact
+  const float rl = fmaf(-k, kPio2C, re) + xl;
+  const float z = rh * rh;
+  const float ps = fmaf(fmaf(fmaf(kRAD_S[3], z, kRAD_S[2]), z, kRAD_S[1]), z, kRAD_S[0]) * rh;
+  const float pc = fmaf(fmaf(fmaf(fmaf(kRAD_C[4], z, kRAD_C[3]), z, kRAD_C[2]), z, kRAD_C[1]), z, kRAD_C[0]);
+  quarter_turn(t, fmaf(rl, pc, ps), fmaf(-rl, ps, pc), s, c);
+}
+
+__device__ __forceinline__ void fsincos(float x, float& s, float& c) { fsincos_c(x, 0.0f, s, c); }
+
 // ------------------------------------------------------------------------------ flow params
 
 constexpr double kPi = 3.14159265358979323846;
@@ -83,8 +140,8 @@ __device__ __forceinline__ void dg_vel32(float piA, float a, float b, float x, f
   float f = fmaf(a, x, b) * x;
   float fx = fmaf(2.0f * a, x, b);
   float sf, cf, sy, cy;
-  sincospif(f, &sf, &cf);
-  sincospif(y, &sy, &cy);
+  fsincospi(f, sf, cf);
+  fsincospi(y, sy, cy);
   u = -piA * sf * cy;
   v = piA * cf * sy * fx;
 }
@@ -98,15 +155,15 @@ __device__ __forceinline__ void dg_vel32c(float piA, float a, float bh, float bl
   float p = a * xh;
   float pe = fmaf(a, xh, -p);  // a xh = p + pe exactly
   float g, ge;
-  two_sum(p, bh, g, ge);       // p + bh = g + ge exactly
+  fast_two_sum(bh, p, g, ge);  // bh + p = g + ge exactly (|bh| >= 1/2 >= |p| on the gyre domain)
   ge = ge + (bl + fmaf(a, xl, pe));  // a x + b = g + ge (to second order)
   float fh = g * xh;
   float fe = fmaf(g, xh, -fh);               // g xh = fh + fe exactly
   float fl = fe + fmaf(ge, xh, g * xl);      // f = fh + fl
   float fx = fmaf(2.0f * a, xh, bh + fmaf(2.0f * a, xl, bl));
   float sf, cf, sy, cy;
-  sincospif(fh, &sf, &cf);
-  sincospif(yh, &sy, &cy);
+  fsincospi(fh, sf, cf);
+  fsincospi(yh, sy, cy);
   float df = kPiF * fl, dy = kPiF * yl;
   float sf2 = fmaf(df, cf, sf), cf2 = fmaf(-df, sf, cf);
   float sy2 = fmaf(dy, cy, sy), cy2 = fmaf(-dy, sy, cy);
@@ -132,27 +189,26 @@ __device__ __forceinline__ void dg_vel64(double A, double eps, double om, double
 __device__ __forceinline__ void abc_vel32(float A, float B, float C, float x, float y, float z,
                                           float& u, float& v, float& w) {
   float sx, cx, sy, cy, sz, cz;
-  sincosf(x, &sx, &cx);
-  sincosf(y, &sy, &cy);
-  sincosf(z, &sz, &cz);
+  fsincos(x, sx, cx);
+  fsincos(y, sy, cy);
+  fsincos(z, sz, cz);
   u = fmaf(A, sz, C * cy);
   v = fmaf(B, sx, A * cz);
   w = fmaf(C, sy, B * cx);
 }
 
+// ABC flow at the compensated point: sin/cos take the low parts (and their own reduction
+// residual) as a first-order correction.
 __device__ __forceinline__ void abc_vel32c(float A, float B, float C, float xh, float xl, float yh,
                                            float yl, float zh, float zl, float& u, float& v,
                                            float& w) {
   float sx, cx, sy, cy, sz, cz;
-  sincosf(xh, &sx, &cx);
-  sincosf(yh, &sy, &cy);
-  sincosf(zh, &sz, &cz);
-  float sx2 = fmaf(xl, cx, sx), cx2 = fmaf(-xl, sx, cx);
-  float sy2 = fmaf(yl, cy, sy), cy2 = fmaf(-yl, sy, cy);
-  float sz2 = fmaf(zl, cz, sz), cz2 = fmaf(-zl, sz, cz);
-  u = fmaf(A, sz2, C * cy2);
-  v = fmaf(B, sx2, A * cz2);
-  w = fmaf(C, sy2, B * cx2);
+  fsincos_c(xh, xl, sx, cx);
+  fsincos_c(yh, yl, sy, cy);
+  fsincos_c(zh, zl, sz, cz);
+  u = fmaf(A, sz, C * cy);
+  v = fmaf(B, sx, A * cz);
+  w = fmaf(C, sy, B * cx);
 }
 
 __device__ __forceinline__ void abc_vel64(double A, double B, double C, double x, double y, double z,

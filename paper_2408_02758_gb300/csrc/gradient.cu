@@ -7,10 +7,12 @@
 //   trigonometric form of the symmetric 3x3 eigenvalues, Smith 1961), FTLE = log1p(mu)/(2|T|)
 //   with mu = lambda_max - 1.
 // It flags a node for the double kernel when float cannot be trusted there: fewer than d
-// neighbours or det(M) <= kCondFlag (tr M/d)^d (ill-conditioned fit), mu < refine_mu
-// (lambda_max - 1 cancels), or in 3D the two largest eigenvalues nearly coincide
-// (1 + r <= kNearDoubleTop, where the trigonometric form loses accuracy).  Flagged nodes are
-// appended to a list with one atomic per warp.
+// neighbours or det(M) <= kCondFlag (tr M/d)^d (ill-conditioned fit); mu < kMuFloor
+// (lambda_max - 1 cancels); ln(lambda_max) h_i < refine_kappa with h_i the RMS neighbour
+// distance (a float flowmap error e shifts F by ~e/h_i, hence the FTLE by ~e/(h_i ln sigma) in
+// relative terms, so these nodes need the float-float re-advection); or in 3D the two largest
+// eigenvalues nearly coincide (1 + r <= kNearDoubleTop, where the trigonometric form loses
+// accuracy).  Flagged nodes are appended to a list with one atomic per warp.
 //
 // Double kernel: the same fit in double for every node (FTLE_PREC_FP64) or for a node list
 // (the fix-up).  mu is the largest eigenvalue of E = F^T F - I formed in double, so it keeps
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(256) k_grad_f32(GradArgs a) {
           for (int c = 0; c < DIM; ++c) b[r * DIM + c] = fmaf(dp[r], dx[c], b[r * DIM + c]);
       }
       float lam = NAN, mu = NAN;
+      const float trm = DIM == 2 ? m[0] + m[2] : m[0] + m[3] + m[5];
       if (re - rs < DIM) {
         flag = true;
       } else if constexpr (DIM == 2) {
@@ -161,8 +164,9 @@ __global__ void __launch_bounds__(256) k_grad_f32(GradArgs a) {
         }
       }
       mu = lam - 1.0f;
-      const bool cancels = (a.refine_mu >= 0.f) && !(mu >= a.refine_mu);
-      flag = flag || cancels || !(lam == lam);
+      const float h_i = sqrtf(trm / (float)(re - rs > 0 ? re - rs : 1));
+      const bool sensitive = (a.refine_kappa >= 0.f) && !(log1pf(mu) * h_i >= a.refine_kappa);
+      flag = flag || !(mu >= kMuFloor) || sensitive || !(lam == lam);
       const float ftle = flag ? NAN : log1pf(mu) * (float)a.inv_2absT;
       reinterpret_cast<float*>(a.ftle_out)[i] = ftle;
       if (a.lam_out) a.lam_out[i] = flag ? NAN : (double)lam;

@@ -20,7 +20,7 @@ struct GradArgs {
   void* ftle_out;              // float [n] (double [n] when out64)
   double* lam_out;             // nullable
   double inv_2absT;            // 1 / (2 |T|)
-  float refine_mu;             // float kernel: flag nodes with lambda_max - 1 < refine_mu
+  float refine_kappa;          // float kernel: flag nodes with ln(lambda_max) * h_i < refine_kappa
   ftle_counters* hdr;
   int32_t* flag_list;          // float kernel appends here
   const int32_t* list;         // double kernel: nullable node list ...
@@ -31,6 +31,7 @@ struct GradArgs {
 constexpr float kCondFlag = 0.02f;       // det(M) <= kCondFlag (tr M / d)^d -> FP64 path
 constexpr float kNearDoubleTop = 1e-3f;  // 3D: 1 + r <= this (two top eigenvalues close) -> FP64
 constexpr double kRankTol = 1e-12;       // FP64: det(M) <= kRankTol (tr M / d)^d -> rank-deficient
+constexpr float kMuFloor = 0.01f;        // lambda_max - 1 below this cancels in float -> FP64
 
 int launch_grad_f32(int dim, int phi_layout, bool coord64, const GradArgs& a, int grid, int block,
                     cudaStream_t stream);

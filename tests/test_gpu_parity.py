@@ -246,3 +246,27 @@ def test_invalid_arguments_raise(F):
     with pytest.raises(F.FTLEError):
         F.ftle_advect(dm, w.flow, 0.0, 1.0, 0.0, "fp32c", phi)
     torch.cuda.synchronize()
+
+
+def test_float_float_readvection_matches_fp64_flowmap(F):
+    """The nodes ftle_refine re-advects (read back from the workspace's list) carry a flowmap
+    that agrees with the FP64 oracle to ~1e-11, i.e. at float-float, not float, accuracy."""
+    import torch
+
+    w = I.preset(1, scale=1 / 16)
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    out = F.compute(dm, w.flow, w.T, w.dt, "fp32c", return_all=True)
+    cnt = F.ftle_read_counters(out["workspace"])
+    n = w.mesh.n_nodes
+    assert cnt["n_readvected"] > 0
+    # workspace layout: 256-byte counters, then int32 flag list [n], then int32 mark list [n]
+    off = 256 + ((4 * n + 255) // 256) * 256
+    ws = out["workspace"].cpu().numpy()
+    marked = np.frombuffer(ws[off: off + 4 * cnt["n_readvected"]].tobytes(), dtype=np.int32)
+    assert len(np.unique(marked)) == len(marked) and marked.min() >= 0 and marked.max() < n
+    ph = out["phi"].double().cpu().numpy()
+    ph = ph[..., 0] + ph[..., 1]
+    ref = O.advect(w.flow.kind, w.flow.params, w.mesh.coords[:, marked], w.T, w.dt)
+    err = np.abs(ph[:, marked] - ref).max()
+    assert err < 1e-10, err
+    torch.cuda.synchronize()
