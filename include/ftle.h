@@ -50,7 +50,8 @@ typedef enum ftle_status {
   FTLE_ECUDA = -2,         /* a CUDA runtime call failed (message in ftle_last_error) */
   FTLE_EWORKSPACE = -3,    /* workspace missing or smaller than the *_workspace_bytes query */
   FTLE_EUNSUPPORTED = -4,  /* combination this build does not provide */
-  FTLE_ERANGE = -5         /* a size beyond a fixed limit (step count, nnz, static capacity) */
+  FTLE_ERANGE = -5,        /* a size beyond a fixed limit (step count, nnz, static capacity) */
+  FTLE_ENOMEM = -6         /* a host-side allocation failed (batch plans) */
 } ftle_status;
 
 /* Velocity fields u(x, t); parameters in ftle_flow.p:
@@ -111,7 +112,8 @@ typedef struct ftle_options {
                              Default 4e-4 when the field is 0; negative turns this test off (the
                              rank, conditioning and lambda_max - 1 < 0.01 checks remain). */
   int32_t advect_block;   /* threads per block of the advection kernel (multiple of 32) */
-  int32_t advect_blocks_per_sm; /* resident blocks per SM the advection grid is sized for */
+  int32_t advect_blocks_per_sm; /* blocks per SM the persistent advection grid is sized for
+                                   (default 2048 / advect_block) */
   int32_t grad_block;     /* threads per block of the gradient kernel (multiple of 32) */
   int32_t grad_tile;      /* nodes per gradient tile (multiple of grad_block) */
   int32_t refine_lanes;   /* re-advection: active lanes per 32-thread block (1..32); fewer lanes

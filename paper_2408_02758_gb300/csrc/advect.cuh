@@ -133,6 +133,137 @@ __device__ __forceinline__ void store_state(void* base, int64_t n, int64_t i, co
   }
 }
 
+// ----------------------------------------------------------------------------- one RK4 step
+
+// Time coefficients of one half step: double gyre a(t), b = bh + bl (float paths) or sin(omega t)
+// (double path); unused by autonomous flows.
+struct Coef {
+  float a, bh, bl;
+  double s;
+};
+
+template <int KIND, int PREC>
+__device__ __forceinline__ Coef coef_at(const float2* tab32, const double* tab64, int m) {
+  Coef c{0.f, 0.f, 0.f, 0.0};
+  if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE) {
+    if constexpr (PREC == P64) {
+      c.s = tab64[m];
+    } else {
+      const float2 t = tab32[m];
+      c.a = t.x;
+      c.bh = fmaf(-2.f, t.x, 1.f);
+      c.bl = t.y;
+    }
+  }
+  return c;
+}
+
+// Position update x + d for the compensated state: TwoSum in general; Fast2Sum for the double
+// gyre, whose velocity vanishes linearly at the walls so that |d| <= |x| always holds.
+template <int KIND>
+__device__ __forceinline__ void comp_add(float xh, float d, float& s, float& e) {
+  if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE) {
+    fast_two_sum(xh, d, s, e);
+  } else {
+    two_sum(xh, d, s, e);
+  }
+}
+
+// Advance one node by one classic RK4 step (stages at t, t + h/2, t + h/2, t + h, with the
+// coefficients c0, c1, c2 of those half steps).  P64 updates xd; P32 updates xh; P32C updates
+// the compensated pair (xh, xl), evaluating the velocity at compensated stage points.
+template <int KIND, int DIM, int PREC>
+__device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const Coef& c1, const Coef& c2,
+                                         float* xh, float* xl, double* xd) {
+  if constexpr (PREC == P64) {
+    double k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], y[DIM];
+    vel_f64<KIND, DIM>(a, xd, c0.s, k1v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) y[d] = fma(0.5 * a.h, k1v[d], xd[d]);
+    vel_f64<KIND, DIM>(a, y, c1.s, k2v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) y[d] = fma(0.5 * a.h, k2v[d], xd[d]);
+    vel_f64<KIND, DIM>(a, y, c1.s, k3v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) y[d] = fma(a.h, k3v[d], xd[d]);
+    vel_f64<KIND, DIM>(a, y, c2.s, k4v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) xd[d] += (a.h / 6.0) * (k1v[d] + 2.0 * (k2v[d] + k3v[d]) + k4v[d]);
+  } else if constexpr (PREC == P32) {
+    float k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], y[DIM];
+    vel_f32<KIND, DIM>(a, xh, c0.a, c0.bh, k1v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) y[d] = fmaf(a.h2_32, k1v[d], xh[d]);
+    vel_f32<KIND, DIM>(a, y, c1.a, c1.bh, k2v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) y[d] = fmaf(a.h2_32, k2v[d], xh[d]);
+    vel_f32<KIND, DIM>(a, y, c1.a, c1.bh, k3v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) y[d] = fmaf(a.h32, k3v[d], xh[d]);
+    vel_f32<KIND, DIM>(a, y, c2.a, c2.bh, k4v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) xh[d] = fmaf(a.h6_32, fmaf(2.f, k2v[d] + k3v[d], k1v[d] + k4v[d]), xh[d]);
+  } else {  // P32C
+    float k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], yh[DIM], yl[DIM];
+    vel_f32c<KIND, DIM>(a, xh, xl, c0.a, c0.bh, c0.bl, k1v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      float e;
+      comp_add<KIND>(xh[d], a.h2_32 * k1v[d], yh[d], e);
+      yl[d] = e + xl[d];
+    }
+    vel_f32c<KIND, DIM>(a, yh, yl, c1.a, c1.bh, c1.bl, k2v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      float e;
+      comp_add<KIND>(xh[d], a.h2_32 * k2v[d], yh[d], e);
+      yl[d] = e + xl[d];
+    }
+    vel_f32c<KIND, DIM>(a, yh, yl, c1.a, c1.bh, c1.bl, k3v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      float e;
+      comp_add<KIND>(xh[d], a.h32 * k3v[d], yh[d], e);
+      yl[d] = e + xl[d];
+    }
+    vel_f32c<KIND, DIM>(a, yh, yl, c2.a, c2.bh, c2.bl, k4v);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const float inc = a.h6_32 * fmaf(2.f, k2v[d] + k3v[d], k1v[d] + k4v[d]);
+      float s, e;
+      comp_add<KIND>(xh[d], inc + xl[d], s, e);
+      xh[d] = s;
+      xl[d] = e;
+    }
+  }
+}
+
+// Fill the shared table with the coefficients of half steps 2 k0 .. 2 k1 (whole block).
+template <int KIND, int PREC>
+__device__ __forceinline__ void build_table(const AdvArgs& a, float2* tab32, double* tab64, int k0, int k1) {
+  if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE) {
+    const double nu = a.p[2] / kPi;  // omega / pi
+    for (int m = threadIdx.x; m <= 2 * (k1 - k0); m += blockDim.x) {
+      if constexpr (PREC == P64) {
+        tab64[m] = sin(a.p[2] * (a.t0 + 0.5 * a.h * (double)(2 * k0 + m)));
+      } else {
+        tab32[m] = dg_coef(a.p[1], nu, a.t0, 0.5 * a.h, 2 * k0 + m);
+      }
+    }
+  }
+}
+
+template <int PREC, int DIM>
+__device__ __forceinline__ void split_state(float* xh, float* xl, const double* xd) {
+  if constexpr (PREC == P64) {
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      xh[d] = (float)xd[d];
+      xl[d] = (float)(xd[d] - (double)xh[d]);
+    }
+  }
+}
+
 // --------------------------------------------------------------------------------- kernel
 
 template <int KIND, int DIM, int PREC, int OUT, typename CT>
@@ -144,8 +275,7 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
 
   const int64_t count = a.list ? (int64_t)*a.list_count : a.n;
   const int nchunks = (a.nsteps + kAdvChunk - 1) / kAdvChunk;
-  const double nu = a.p[2] / kPi;  // omega / pi (double gyre)
-  bool table_valid = false;        // single-chunk tables are built once per block
+  bool table_valid = false;  // single-chunk tables are built once per block
 
   const int lanes = (a.lanes > 0 && a.lanes < (int)blockDim.x) ? a.lanes : (int)blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * lanes; base < count; base += (int64_t)gridDim.x * lanes) {
@@ -157,14 +287,12 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
     double xd[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      double c = active ? load_coord<CT>(a.coords, d * a.n_mesh + i) : 0.0;
+      const double c = active ? load_coord<CT>(a.coords, d * a.n_mesh + i) : 0.0;
       xd[d] = c;
       xh[d] = (float)c;
       xl[d] = (float)(c - (double)xh[d]);
     }
-    if (a.ckpt && active) {
-      store_state<OUT, DIM>(a.ckpt, a.n_mesh, i, xh, xl, xd);
-    }
+    if (a.ckpt && active) store_state<OUT, DIM>(a.ckpt, a.n_mesh, i, xh, xl, xd);
     int ck_left = a.ckpt_every;
     int ck_slot = 1;
 
@@ -174,13 +302,7 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
       if constexpr (kTable) {
         if (!(table_valid && nchunks == 1)) {
           __syncthreads();
-          for (int m = threadIdx.x; m <= 2 * (k1 - k0); m += blockDim.x) {
-            if constexpr (PREC == P64) {
-              tab64[m] = sin(a.p[2] * (a.t0 + 0.5 * a.h * (double)(2 * k0 + m)));
-            } else {
-              tab32[m] = dg_coef(a.p[1], nu, a.t0, 0.5 * a.h, 2 * k0 + m);
-            }
-          }
+          build_table<KIND, PREC>(a, tab32, tab64, k0, k1);
           __syncthreads();
           table_valid = true;
         }
@@ -188,99 +310,14 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
       if (!active) continue;
       for (int k = k0; k < k1; ++k) {
         const int m = 2 * (k - k0);
-        if constexpr (PREC == P64) {
-          double s0 = 0, s1 = 0, s2 = 0;
-          if constexpr (kTable) {
-            s0 = tab64[m];
-            s1 = tab64[m + 1];
-            s2 = tab64[m + 2];
-          }
-          double k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], y[DIM];
-          vel_f64<KIND, DIM>(a, xd, s0, k1v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) y[d] = fma(0.5 * a.h, k1v[d], xd[d]);
-          vel_f64<KIND, DIM>(a, y, s1, k2v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) y[d] = fma(0.5 * a.h, k2v[d], xd[d]);
-          vel_f64<KIND, DIM>(a, y, s1, k3v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) y[d] = fma(a.h, k3v[d], xd[d]);
-          vel_f64<KIND, DIM>(a, y, s2, k4v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d)
-            xd[d] += (a.h / 6.0) * (k1v[d] + 2.0 * (k2v[d] + k3v[d]) + k4v[d]);
-        } else if constexpr (PREC == P32) {
-          float c0a = 0, c0b = 0, c1a = 0, c1b = 0, c2a = 0, c2b = 0;
-          if constexpr (kTable) {
-            float2 t0 = tab32[m], t1 = tab32[m + 1], t2 = tab32[m + 2];
-            c0a = t0.x; c0b = fmaf(-2.f, t0.x, 1.f);
-            c1a = t1.x; c1b = fmaf(-2.f, t1.x, 1.f);
-            c2a = t2.x; c2b = fmaf(-2.f, t2.x, 1.f);
-          }
-          float k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], y[DIM];
-          vel_f32<KIND, DIM>(a, xh, c0a, c0b, k1v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) y[d] = fmaf(a.h2_32, k1v[d], xh[d]);
-          vel_f32<KIND, DIM>(a, y, c1a, c1b, k2v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) y[d] = fmaf(a.h2_32, k2v[d], xh[d]);
-          vel_f32<KIND, DIM>(a, y, c1a, c1b, k3v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) y[d] = fmaf(a.h32, k3v[d], xh[d]);
-          vel_f32<KIND, DIM>(a, y, c2a, c2b, k4v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d)
-            xh[d] = fmaf(a.h6_32, fmaf(2.f, k2v[d] + k3v[d], k1v[d] + k4v[d]), xh[d]);
-        } else {  // P32C
-          float c0a = 0, c0h = 0, c0l = 0, c1a = 0, c1h = 0, c1l = 0, c2a = 0, c2h = 0, c2l = 0;
-          if constexpr (kTable) {
-            float2 t0 = tab32[m], t1 = tab32[m + 1], t2 = tab32[m + 2];
-            c0a = t0.x; c0h = fmaf(-2.f, t0.x, 1.f); c0l = t0.y;
-            c1a = t1.x; c1h = fmaf(-2.f, t1.x, 1.f); c1l = t1.y;
-            c2a = t2.x; c2h = fmaf(-2.f, t2.x, 1.f); c2l = t2.y;
-          }
-          float k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], yh[DIM], yl[DIM];
-          vel_f32c<KIND, DIM>(a, xh, xl, c0a, c0h, c0l, k1v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            float e;
-            two_sum(xh[d], a.h2_32 * k1v[d], yh[d], e);
-            yl[d] = e + xl[d];
-          }
-          vel_f32c<KIND, DIM>(a, yh, yl, c1a, c1h, c1l, k2v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            float e;
-            two_sum(xh[d], a.h2_32 * k2v[d], yh[d], e);
-            yl[d] = e + xl[d];
-          }
-          vel_f32c<KIND, DIM>(a, yh, yl, c1a, c1h, c1l, k3v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            float e;
-            two_sum(xh[d], a.h32 * k3v[d], yh[d], e);
-            yl[d] = e + xl[d];
-          }
-          vel_f32c<KIND, DIM>(a, yh, yl, c2a, c2h, c2l, k4v);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            float inc = a.h6_32 * fmaf(2.f, k2v[d] + k3v[d], k1v[d] + k4v[d]);
-            float s, e;
-            two_sum(xh[d], inc + xl[d], s, e);
-            xh[d] = s;
-            xl[d] = e;
-          }
-        }
+        const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
+        const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
+        const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
+        rk4_step<KIND, DIM, PREC>(a, c0, c1, c2, xh, xl, xd);
         if (a.ckpt) {
           if (--ck_left == 0) {
             ck_left = a.ckpt_every;
-            if constexpr (PREC == P64) {
-#pragma unroll
-              for (int d = 0; d < DIM; ++d) {
-                xh[d] = (float)xd[d];
-                xl[d] = (float)(xd[d] - (double)xh[d]);
-              }
-            }
+            split_state<PREC, DIM>(xh, xl, xd);
             store_state<OUT, DIM>(reinterpret_cast<char*>(a.ckpt) + (int64_t)ck_slot * a.ckpt_stride_bytes,
                                   a.n_mesh, i, xh, xl, xd);
             ++ck_slot;
@@ -289,13 +326,7 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
       }
     }
     if (active) {
-      if constexpr (PREC == P64) {
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          xh[d] = (float)xd[d];
-          xl[d] = (float)(xd[d] - (double)xh[d]);
-        }
-      }
+      split_state<PREC, DIM>(xh, xl, xd);
       store_state<OUT, DIM>(a.out, a.n_mesh, i, xh, xl, xd);
     }
   }

@@ -4,6 +4,7 @@
 // few warps spread over the SM sub-partitions.  The double-gyre coefficient a(t) is tabulated
 // per block in double and split into float-float.
 #include "advect.cuh"
+#include "batch.cuh"
 #include "capi_internal.cuh"
 #include "dsfloat.cuh"
 
@@ -125,6 +126,77 @@ __global__ void __launch_bounds__(32) k_advect_ds(AdvArgs a) {
       for (int d = 0; d < DIM; ++d) o[d * a.n_mesh + i] = make_float2(x[d].h, x[d].l);
     }
   }
+}
+
+// Batched re-advection: the list holds (instance, node) pairs, so lanes of one warp may belong
+// to different instances; each lane forms its own double-gyre coefficient a(t_m) =
+// eps sin(omega t_m) in float-float (t_m = t0 + m h/2) instead of reading a shared table.
+template <int KIND, int DIM>
+__global__ void __launch_bounds__(32) k_batch_advect_ds(const BatchInst* __restrict__ insts, const int2* pairs,
+                                                        const unsigned long long* count) {
+  const int64_t cnt = (int64_t)*count;
+  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < cnt;
+       slot += (int64_t)gridDim.x * blockDim.x) {
+    const int2 pr = pairs[slot];
+    const AdvArgs a = insts[pr.x].adv;
+    const int64_t i = pr.y;
+    DsFlow F;
+    if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE) {
+      F.c[0] = ds_from_double(kPi * a.p[0]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) F.c[q] = ds_from_double(a.p[q]);
+    }
+    const dsf h = ds_from_double(a.h), h2 = ds_from_double(0.5 * a.h), h6 = ds_from_double(a.h / 6.0);
+    const dsf eps = ds_from_double(a.p[1]), omega = ds_from_double(a.p[2]);
+    auto coef = [&](int m) -> dsf {
+      if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE) {
+        dsf s, c;
+        ds_sincos(ds_mul(omega, ds_from_double(a.t0 + 0.5 * a.h * (double)m)), s, c);
+        return ds_mul(eps, s);
+      } else {
+        return ds_make(0.f, 0.f);
+      }
+    };
+    dsf x[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) x[d] = ds_from_double((double)__ldg(reinterpret_cast<const float*>(a.coords) + d * a.n_mesh + i));
+    dsf c2 = coef(0);
+    for (int k = 0; k < a.nsteps; ++k) {
+      const dsf c0 = c2, c1 = coef(2 * k + 1);
+      c2 = coef(2 * k + 2);
+      dsf k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], y[DIM];
+      vel_ds<KIND, DIM>(F, x, c0, k1v);
+      ds_axpy<DIM>(x, h2, k1v, y);
+      vel_ds<KIND, DIM>(F, y, c1, k2v);
+      ds_axpy<DIM>(x, h2, k2v, y);
+      vel_ds<KIND, DIM>(F, y, c1, k3v);
+      ds_axpy<DIM>(x, h, k3v, y);
+      vel_ds<KIND, DIM>(F, y, c2, k4v);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const dsf s23 = ds_add(k2v[d], k3v[d]);
+        const dsf s = ds_add(ds_add(k1v[d], k4v[d]), ds_make(2.0f * s23.h, 2.0f * s23.l));
+        x[d] = ds_add(x[d], ds_mul(h6, s));
+      }
+    }
+    float2* o = reinterpret_cast<float2*>(a.out);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o[d * a.n_mesh + i] = make_float2(x[d].h, x[d].l);
+  }
+}
+
+int launch_batch_advect_ds(int kind, int dim, const BatchInst* insts, const int2* pairs,
+                           const unsigned long long* count, int grid, int block, cudaStream_t s) {
+  if (kind == FTLE_FLOW_DOUBLE_GYRE && dim == 2) k_batch_advect_ds<FTLE_FLOW_DOUBLE_GYRE, 2><<<grid, block, 0, s>>>(insts, pairs, count);
+  else if (kind == FTLE_FLOW_ABC && dim == 3) k_batch_advect_ds<FTLE_FLOW_ABC, 3><<<grid, block, 0, s>>>(insts, pairs, count);
+  else if (kind == FTLE_FLOW_LINEAR && dim == 2) k_batch_advect_ds<FTLE_FLOW_LINEAR, 2><<<grid, block, 0, s>>>(insts, pairs, count);
+  else if (kind == FTLE_FLOW_LINEAR && dim == 3) k_batch_advect_ds<FTLE_FLOW_LINEAR, 3><<<grid, block, 0, s>>>(insts, pairs, count);
+  else if (kind == FTLE_FLOW_SADDLE && dim == 2) k_batch_advect_ds<FTLE_FLOW_SADDLE, 2><<<grid, block, 0, s>>>(insts, pairs, count);
+  else if (kind == FTLE_FLOW_SADDLE && dim == 3) k_batch_advect_ds<FTLE_FLOW_SADDLE, 3><<<grid, block, 0, s>>>(insts, pairs, count);
+  else return fail(FTLE_EUNSUPPORTED, "batched float-float advection: flow %d in %dD", kind, dim);
+  FTLE_LAUNCH_CHECK("k_batch_advect_ds launch");
+  return FTLE_OK;
 }
 
 template <int KIND, int DIM>

@@ -144,7 +144,7 @@ int check_launch(const Launch& L) {
     return fail(FTLE_EINVAL, "advect_block must be a multiple of 32 in [32, 256]");
   if (L.grad_block % 32 || L.grad_block < 32 || L.grad_block > 256)
     return fail(FTLE_EINVAL, "grad_block must be a multiple of 32 in [32, 256]");
-  if (L.advect_bps < 1 || L.advect_bps > 64) return fail(FTLE_EINVAL, "advect_blocks_per_sm in [1, 64]");
+  if (L.advect_bps < 0 || L.advect_bps > 64) return fail(FTLE_EINVAL, "advect_blocks_per_sm in [0, 64]");
   if (L.refine_lanes < 1 || L.refine_lanes > 32) return fail(FTLE_EINVAL, "refine_lanes in [1, 32]");
   return FTLE_OK;
 }
@@ -272,7 +272,7 @@ int run_advect(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
   const int out = precision == FTLE_PREC_FP64 ? O64 : (precision == FTLE_PREC_FP32 ? O32 : O32PAIR);
   int block = L.advect_block;
   if (prec == P64 && block > 128) block = 128;
-  const int grid = grid_for(m->n_nodes, block, L.advect_bps * 256 / block);
+  const int grid = grid_for(m->n_nodes, block, L.advect_bps > 0 ? L.advect_bps : 2048 / block);
   return launch_advect(fl->kind, m->dim, prec, out, m->coord_fp64 != 0, a, grid, block, s);
 }
 
@@ -296,6 +296,7 @@ const char* ftle_status_string(int status) {
     case FTLE_EWORKSPACE: return "workspace missing, misaligned or too small";
     case FTLE_EUNSUPPORTED: return "unsupported combination";
     case FTLE_ERANGE: return "size beyond a fixed limit";
+    case FTLE_ENOMEM: return "host allocation failed";
     default: return "unknown status";
   }
 }

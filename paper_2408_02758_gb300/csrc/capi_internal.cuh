@@ -10,7 +10,7 @@ namespace ftle {
 struct Launch {
   double refine_kappa = 4e-4;
   int advect_block = 256;
-  int advect_bps = 8;     // resident blocks per SM for 256-thread blocks (scaled for others)
+  int advect_bps = 0;     // resident blocks per SM the advection grid is sized for (0: 2048/block)
   int grad_block = 256;
   int refine_lanes = 32;
 };

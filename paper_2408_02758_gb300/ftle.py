@@ -21,7 +21,7 @@ import numpy as np
 from . import _build
 
 PREC = {"fp64": 0, "fp32": 1, "fp32c": 2}
-FTLE_OK, FTLE_EINVAL, FTLE_ECUDA, FTLE_EWORKSPACE, FTLE_EUNSUPPORTED, FTLE_ERANGE = 0, -1, -2, -3, -4, -5
+FTLE_OK, FTLE_EINVAL, FTLE_ECUDA, FTLE_EWORKSPACE, FTLE_EUNSUPPORTED, FTLE_ERANGE, FTLE_ENOMEM = 0, -1, -2, -3, -4, -5, -6
 
 
 class ftle_mesh(Structure):
@@ -327,3 +327,63 @@ def compute(mesh: DeviceMesh, flow, T: float, dt: float, precision="fp32c", t0: 
     if return_all:
         return {"ftle": out, "lam": lam, "phi": phi, "workspace": ws}
     return out
+
+
+# ------------------------------------------------------------------------------ batched
+
+
+def _batch_arrays(meshes, flows, T, outs):
+    n = len(meshes)
+    if not (len(flows) == len(T) == len(outs) == n):
+        raise ValueError("meshes, flows, T and outs must have the same length")
+    M = (ftle_mesh * n)(*[m.desc for m in meshes])
+    Fl = (ftle_flow * n)(*[make_flow(f) for f in flows])
+    Ta = (c_double * n)(*[float(t) for t in T])
+    Oa = (c_void_p * n)(*[_ptr(o) for o in outs])
+    return n, M, Fl, Ta, Oa
+
+
+def ftle_batch_workspace_bytes(meshes, precision) -> int:
+    n = len(meshes)
+    M = (ftle_mesh * n)(*[m.desc for m in meshes])
+    return int(lib().ftle_batch_workspace_bytes(n, M, _prec(precision)))
+
+
+def ftle_batch(meshes, flows, T, dt: float, precision, outs, workspace, options: ftle_options | None = None,
+               stream=None):
+    """FTLE of many independent problems in one launch sequence (instances share dt, precision,
+    dimension and flow kind).  ``outs`` are device float tensors, one per instance."""
+    n, M, Fl, Ta, Oa = _batch_arrays(meshes, flows, T, outs)
+    _check("ftle_batch", lib().ftle_batch(n, M, Fl, Ta, dt, _prec(precision), Oa, _ptr(workspace),
+                                          workspace.numel() * workspace.element_size(),
+                                          ctypes.byref(options) if options else None, _stream(stream)))
+
+
+class BatchPlan:
+    """A batch captured once into a CUDA graph (ftle_batch_plan_create) and replayed with launch()."""
+
+    def __init__(self, meshes, flows, T, dt: float, precision, outs, workspace,
+                 options: ftle_options | None = None, stream=None):
+        n, M, Fl, Ta, Oa = _batch_arrays(meshes, flows, T, outs)
+        self._keep = (meshes, outs, workspace)
+        h = c_void_p()
+        _check("ftle_batch_plan_create",
+               lib().ftle_batch_plan_create(n, M, Fl, Ta, dt, _prec(precision), Oa, _ptr(workspace),
+                                            workspace.numel() * workspace.element_size(),
+                                            ctypes.byref(options) if options else None, _stream(stream),
+                                            ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check("ftle_batch_plan_launch", lib().ftle_batch_plan_launch(self.handle, _stream(stream)))
+
+    def destroy(self):
+        if self.handle:
+            lib().ftle_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -1,0 +1,116 @@
+"""Batched execution (ftle_batch, ftle_batch_plan_*) on the GPU: every instance equals its
+single-problem result (same kernels' arithmetic), the captured graph replays identically, and
+instances match the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2408_02758_gb300 import inputs as I
+
+from _parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def batch():
+    import torch
+
+    from paper_2408_02758_gb300 import ftle
+
+    ws_list = I.batched_preset(12, scale=1 / 8)  # 8x4 .. 128x64 grids, T in {5, 10, 15, 20}
+    meshes = [ftle.DeviceMesh.from_mesh(w.mesh) for w in ws_list]
+    outs = [torch.full((w.mesh.n_nodes,), 7.0, dtype=torch.float32, device="cuda") for w in ws_list]
+    return ftle, torch, ws_list, meshes, outs
+
+
+def _single(ftle, w, dm, options=None):
+    out = ftle.compute(dm, w.flow, w.T, w.dt, "fp32c", return_all=True, options=options)
+    return out["ftle"].double().cpu().numpy(), ftle.ftle_read_counters(out["workspace"])
+
+
+@pytest.mark.parametrize("kappa", [0.0, 0.05])
+def test_batch_equals_single_instances(batch, kappa):
+    """kappa = 0 is the default flagging; 0.05 forces the re-advection path on many nodes."""
+    ftle, torch, ws_list, meshes, outs = batch
+    opt = ftle.make_options(refine_kappa=kappa)
+    ws = ftle.workspace_empty(ftle.ftle_batch_workspace_bytes(meshes, "fp32c"))
+    ftle.ftle_batch(meshes, [w.flow for w in ws_list], [w.T for w in ws_list], 0.01, "fp32c", outs, ws, options=opt)
+    torch.cuda.synchronize()
+    n_refined = 0
+    for w, dm, o in zip(ws_list, meshes, outs):
+        single, cnt = _single(ftle, w, dm, opt)
+        got = o.double().cpu().numpy()
+        # identical arithmetic except the float-float time coefficients of re-advected nodes
+        same = got == single
+        assert np.all(same | (np.abs(got - single) <= 1e-9 * np.abs(single))), w.name
+        n_refined += cnt["n_readvected"]
+    if kappa > 0:
+        assert n_refined > 0  # the refinement path ran
+
+
+def test_batch_plan_graph_replays_identically(batch):
+    ftle, torch, ws_list, meshes, outs = batch
+    ws = ftle.workspace_empty(ftle.ftle_batch_workspace_bytes(meshes, "fp32c"))
+    ftle.ftle_batch(meshes, [w.flow for w in ws_list], [w.T for w in ws_list], 0.01, "fp32c", outs, ws)
+    torch.cuda.synchronize()
+    ref = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(-1.0)
+    plan = ftle.BatchPlan(meshes, [w.flow for w in ws_list], [w.T for w in ws_list], 0.01, "fp32c", outs, ws,
+                          options=ftle.make_options(grad_tile=512))
+    for _ in range(2):
+        plan.launch()
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            assert torch.equal(o, r)
+        for o in outs:
+            o.fill_(-1.0)
+    plan.destroy()
+
+
+def test_batch_instances_match_oracle(batch):
+    ftle, torch, ws_list, meshes, outs = batch
+    ws = ftle.workspace_empty(ftle.ftle_batch_workspace_bytes(meshes, "fp32c"))
+    ftle.ftle_batch(meshes, [w.flow for w in ws_list], [w.T for w in ws_list], 0.01, "fp32c", outs, ws)
+    torch.cuda.synchronize()
+    for k in (0, 3, 7):
+        w = ws_list[k]
+        o = O.ftle(w.flow.kind, w.flow.params, w.mesh.coords, w.mesh.row_ptr, w.mesh.col_idx, w.T, w.dt)
+        rep = compare(outs[k].double().cpu().numpy(), o["ftle"], o["lam"])
+        assert rep["ok"], (w.name, rep)
+
+
+def test_batch_rejects_mixed_dimensions(batch):
+    ftle, torch, ws_list, meshes, outs = batch
+    m3 = I.make_mesh((4, 4, 4), (0, 0, 0), (1, 1, 1), I.KUHN, 0.2, 3)
+    d3 = ftle.DeviceMesh.from_mesh(m3)
+    o3 = torch.empty(m3.n_nodes, device="cuda")
+    ws = ftle.workspace_empty(ftle.ftle_batch_workspace_bytes([meshes[0], d3], "fp32c"))
+    with pytest.raises(ftle.FTLEError) as e:
+        ftle.ftle_batch([meshes[0], d3], [ws_list[0].flow, I.FlowSpec.abc()], [1.0, 1.0], 0.01, "fp32c",
+                        [outs[0], o3], ws)
+    assert e.value.status == ftle.FTLE_EINVAL
+
+
+def test_autotuned_options_give_identical_results(batch):
+    """Launch shapes change scheduling only: the tuned options reproduce the default result."""
+    ftle, torch, ws_list, meshes, outs = batch
+    from paper_2408_02758_gb300 import autotune
+
+    w = I.preset(1, scale=1 / 16)
+    dm = ftle.DeviceMesh.from_mesh(w.mesh)
+    cache = autotune.Cache(autotune.cache_path().with_name("autotune_test.json"))
+    opts = autotune.options_for_compute(dm, w.flow, w.T, w.dt, "fp32c", cache=cache, retune=True)
+    a = ftle.compute(dm, w.flow, w.T, w.dt, "fp32c").cpu()
+    b = ftle.compute(dm, w.flow, w.T, w.dt, "fp32c", options=opts).cpu()
+    assert torch.equal(a, b)
+    bopt = autotune.options_for_batch(meshes, [x.flow for x in ws_list], [x.T for x in ws_list], 0.01, "fp32c",
+                                      cache=cache, retune=True)
+    ws = ftle.workspace_empty(ftle.ftle_batch_workspace_bytes(meshes, "fp32c"))
+    ftle.ftle_batch(meshes, [x.flow for x in ws_list], [x.T for x in ws_list], 0.01, "fp32c", outs, ws)
+    ref = [o.clone() for o in outs]
+    ftle.ftle_batch(meshes, [x.flow for x in ws_list], [x.T for x in ws_list], 0.01, "fp32c", outs, ws, options=bopt)
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
