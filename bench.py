@@ -269,6 +269,74 @@ def run_batched(args, world, rank, local):
         "clocks": clk, "gpu_launches": 7 * K, "cpu_baseline": None, "e2e": None}), flush=True)
 
 
+# ----------------------------------------------------------------------------- differentiable workload
+
+
+def run_differentiable(args, world, rank, local):
+    """d(region-mean FTLE)/d(A, eps, omega) on the 1024 x 512 jittered triangle mesh, T = 15,
+    checkpoints every 50 steps: forward (advection with checkpoints, FTLE core, refinement) plus
+    the reverse-mode adjoint, against the plain forward path on the same GPU."""
+    import numpy as np
+    import torch
+
+    from paper_2408_02758_gb300 import ftle
+    from paper_2408_02758_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ftle.lib()
+    w = I.preset(4, scale=args.scale)
+    n = w.mesh.n_nodes
+    ce = w.extra["ckpt_every"]
+    dm = ftle.DeviceMesh.from_mesh(w.mesh, device=dev)
+    wt = torch.from_numpy(w.extra["weights"]).float().to(dev)
+    phi = ftle.flowmap_empty(2, n, "fp32c", device=dev)
+    ck = ftle.checkpoints_empty(2, n, w.n_steps, ce, "fp32c", device=dev)
+    out = ftle.ftle_out_empty(n, "fp32c", device=dev)
+    ws = ftle.workspace_empty(ftle.ftle_workspace_bytes(n), device=dev)
+    bws = ftle.workspace_empty(ftle.ftle_backward_workspace_bytes(n, 2), device=dev)
+    grad = torch.empty(3, dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    K, W = args.steps, args.warmup
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(W + K)]
+    with torch.cuda.stream(stream):
+        for k in range(W + K):
+            if k == W:
+                torch.cuda.synchronize()
+                clocks = ClockSampler(None)
+                clocks.start()
+                time.sleep(0.3)
+            flush.fill_(float(k))
+            e = ev[k]
+            e[0].record(stream)  # plain forward
+            ftle.ftle_compute(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi, out, None, ws, stream=sh)
+            e[1].record(stream)
+            flush.fill_(float(k))
+            e[2].record(stream)  # forward with checkpoints + backward
+            ftle.ftle_advect(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi, ck, ce, stream=sh)
+            ftle.ftle_gradient_eig(dm, phi, "fp32c", w.T, out, None, ws, stream=sh)
+            ftle.ftle_refine(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi, out, None, ws, stream=sh)
+            ftle.ftle_backward(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi, ck, ce, wt, grad, bws, stream=sh)
+            e[3].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+    fwd = statistics.mean(ev[k][0].elapsed_time(ev[k][1]) for k in range(W, W + K))
+    both = statistics.mean(ev[k][2].elapsed_time(ev[k][3]) for k in range(W, W + K))
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC + " and d(region-mean FTLE)/d(A,eps,omega)", "value": n / (both / 1000), "unit": UNIT,
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": both, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "nodes": n, "steps_rk4": w.n_steps, "ckpt_every": ce, "precision": "fp32c",
+                   "loss": "mean FTLE over nodes with x0 in [0.5, 1.5]", "l2": "flushed between steps"},
+        "forward_only_ms": fwd, "forward_plus_backward_ms": both, "backward_over_forward": (both - fwd) / fwd,
+        "gradient": grad.cpu().tolist(), "clocks": clk, "gpu_launches": 9 * K, "cpu_baseline": None, "e2e": None,
+        "roofline": None}), flush=True)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 
@@ -292,6 +360,9 @@ def main():
 
     if args.workload == 3:
         run_batched(args, world, rank, local)
+        return
+    if args.workload == 4 and args.impl == "ours":
+        run_differentiable(args, world, rank, local)
         return
     w = I.preset(args.workload, scale=args.scale)
 

@@ -387,3 +387,31 @@ class BatchPlan:
             self.destroy()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------------------ differentiation
+
+
+def ftle_backward_workspace_bytes(n_nodes: int, dim: int = 2) -> int:
+    return int(lib().ftle_backward_workspace_bytes(n_nodes, dim))
+
+
+def ftle_backward(mesh: DeviceMesh, flow, t0: float, T: float, dt: float, precision, flowmap, checkpoints,
+                  ckpt_every: int, dL_dftle, dL_dparams, workspace, options: ftle_options | None = None,
+                  stream=None):
+    """d(sum_i dL_dftle[i] FTLE_i)/d(A, eps, omega) into dL_dparams (device float64 [3])."""
+    f = make_flow(flow)
+    _check("ftle_backward",
+           lib().ftle_backward(ctypes.byref(mesh.desc), ctypes.byref(f), t0, T, dt, _prec(precision), _ptr(flowmap),
+                               _ptr(checkpoints), ckpt_every, _ptr(dL_dftle), _ptr(dL_dparams), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(),
+                               ctypes.byref(options) if options else None, _stream(stream)))
+
+
+def checkpoints_empty(dim: int, n_nodes: int, n_steps: int, ckpt_every: int, precision, device="cuda"):
+    """Checkpoint slots for ftle_advect: n_steps // ckpt_every + 1 flowmaps."""
+    import torch
+
+    slots = n_steps // ckpt_every + 1
+    one = flowmap_empty(dim, n_nodes, precision, device=device)
+    return torch.empty((slots,) + tuple(one.shape), dtype=one.dtype, device=device)

@@ -1,0 +1,94 @@
+"""Reverse-mode derivative of a weighted FTLE sum with respect to the double-gyre parameters
+(ftle_backward / FTLEFunction) against the FP64 oracle's forward-mode derivative (itself pinned
+to Richardson-extrapolated central differences) and against central differences of the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2408_02758_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _region_weights(mesh):
+    x0 = mesh.coords[0].astype(np.float64)
+    r = ((x0 >= 0.5) & (x0 <= 1.5)).astype(np.float64)
+    return r / r.sum()
+
+
+@pytest.mark.parametrize("scale,T,ckpt", [(1 / 16, 5.0, 50), (1 / 8, 15.0, 50), (1 / 16, 3.0, 7)])
+def test_adjoint_matches_oracle_tangent_linear(scale, T, ckpt):
+    import torch
+
+    from paper_2408_02758_gb300 import ftle
+    from paper_2408_02758_gb300.autograd import ftle_field
+
+    w = I.preset(4, scale=scale)  # jittered triangle mesh over [0,2] x [0,1], double gyre
+    dm = ftle.DeviceMesh.from_mesh(w.mesh)
+    wts = _region_weights(w.mesh)
+    p0 = w.flow.params[:3].copy()
+    params = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    field = ftle_field(params, dm, T, w.dt, "fp32c", ckpt)
+    loss = (field.double().cpu() * torch.from_numpy(wts)).sum()
+    loss.backward()
+    g_gpu = params.grad.numpy()
+    g_orc, ft = O.param_grad(w.mesh.coords.astype(np.float64), w.mesh.row_ptr, w.mesh.col_idx, p0, T, w.dt, wts)
+    rel = np.abs(g_gpu - g_orc) / np.maximum(np.abs(g_orc), 1e-3 * np.abs(g_orc).max())
+    print("gpu", g_gpu, "oracle", g_orc, "rel", rel)
+    assert np.all(rel < 2e-3), (g_gpu, g_orc, rel)
+    assert abs(loss.item() - float(wts @ ft)) < 1e-4 * abs(float(wts @ ft))
+
+
+def test_adjoint_matches_oracle_central_differences():
+    import torch
+
+    from paper_2408_02758_gb300 import ftle
+    from paper_2408_02758_gb300.autograd import ftle_field
+
+    w = I.preset(4, scale=1 / 16)
+    T = 4.0
+    dm = ftle.DeviceMesh.from_mesh(w.mesh)
+    wts = _region_weights(w.mesh)
+    p0 = w.flow.params[:3].copy()
+    params = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    loss = (ftle_field(params, dm, T, w.dt).double().cpu() * torch.from_numpy(wts)).sum()
+    loss.backward()
+    x0 = w.mesh.coords.astype(np.float64)
+    h = 1e-4
+    for q in range(3):
+        e = np.zeros(3)
+        e[q] = h
+        fp = O.ftle(O.DOUBLE_GYRE, p0 + e, x0, w.mesh.row_ptr, w.mesh.col_idx, T, w.dt)["ftle"]
+        fm = O.ftle(O.DOUBLE_GYRE, p0 - e, x0, w.mesh.row_ptr, w.mesh.col_idx, T, w.dt)["ftle"]
+        fd = (wts @ fp - wts @ fm) / (2 * h)
+        assert abs(params.grad[q].item() - fd) <= 3e-3 * max(abs(fd), 1e-2), (q, params.grad[q].item(), fd)
+
+
+def test_backward_is_deterministic_and_validates():
+    import torch
+
+    from paper_2408_02758_gb300 import ftle
+
+    w = I.preset(4, scale=1 / 16)
+    dm = ftle.DeviceMesh.from_mesh(w.mesh)
+    n = w.mesh.n_nodes
+    T, ce = 2.0, 50
+    phi = ftle.flowmap_empty(2, n, "fp32c")
+    ck = ftle.checkpoints_empty(2, n, 200, ce, "fp32c")
+    ftle.ftle_advect(dm, w.flow, 0.0, T, w.dt, "fp32c", phi, ck, ce)
+    wt = torch.from_numpy(_region_weights(w.mesh)).float().cuda()
+    ws = ftle.workspace_empty(ftle.ftle_backward_workspace_bytes(n, 2))
+    outs = []
+    for _ in range(2):
+        d = torch.empty(3, dtype=torch.float64, device="cuda")
+        ftle.ftle_backward(dm, w.flow, 0.0, T, w.dt, "fp32c", phi, ck, ce, wt, d, ws)
+        outs.append(d.cpu())
+    assert torch.equal(outs[0], outs[1])
+    with pytest.raises(ftle.FTLEError) as e:
+        ftle.ftle_backward(dm, I.FlowSpec.saddle(), 0.0, T, w.dt, "fp32c", phi, ck, ce, wt, outs[0].cuda(), ws)
+    assert e.value.status == ftle.FTLE_EUNSUPPORTED
+    with pytest.raises(ftle.FTLEError) as e:
+        ftle.ftle_backward(dm, w.flow, 0.0, T, w.dt, "fp32c", phi, ck, 0, wt, outs[0].cuda(), ws)
+    assert e.value.status == ftle.FTLE_EINVAL
