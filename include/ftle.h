@@ -87,6 +87,14 @@ typedef struct ftle_mesh {
   const void* coords;     /* device, SoA [dim][n_nodes] */
   const int32_t* row_ptr; /* device [n_nodes + 1], non-decreasing, row_ptr[0] = 0 */
   const int32_t* col_idx; /* device [nnz] */
+  /* Optional fixed-width form of the same lists, the paper's decoupled layout (Section 2.2):
+   * ell_idx[s * n_nodes + i] is neighbour s of node i, -1 where a node has fewer than ell_width
+   * neighbours.  When set (ell_width > 0, ell_idx != NULL) the float gradient kernel reads it
+   * instead of the CSR rows (all slot loads independent and coalesced); the CSR arrays stay
+   * required for the FP64 path, the refinement and the adjoint.  Build it with ftle_ell_from_csr. */
+  int32_t ell_width;      /* 0: no fixed-width list */
+  int32_t reserved;       /* must be 0 */
+  const int32_t* ell_idx; /* device [ell_width][n_nodes] or NULL */
 } ftle_mesh;
 
 typedef struct ftle_flow {
@@ -185,6 +193,11 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
                       const ftle_flow* flow, double t0, double T, double dt, int32_t precision,
                       void* ftle_host, void* device_ws, size_t device_ws_bytes,
                       const ftle_options* opt, void* stream);
+
+/* Fixed-width neighbour list from the CSR rows of `mesh` into ell_idx ([width][n_nodes] int32,
+ * device, caller-owned), -1 padded.  Reads row_ptr back to the host to check that no row is
+ * longer than `width` (FTLE_ERANGE otherwise; nothing launched), then fills ell_idx on `stream`. */
+int ftle_ell_from_csr(const ftle_mesh* mesh, int32_t width, int32_t* ell_idx, void* stream);
 
 /* Synchronous read of the counters at the start of `workspace` (waits for `stream`). */
 int ftle_read_counters(const void* workspace, ftle_counters* out, void* stream);

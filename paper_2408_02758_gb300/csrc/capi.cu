@@ -8,6 +8,7 @@
 
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "advect.cuh"
 #include "capi_internal.cuh"
@@ -80,6 +81,8 @@ int check_mesh(const ftle_mesh* m) {
   if (m->coord_fp64 != 0 && m->coord_fp64 != 1) return fail(FTLE_EINVAL, "coord_fp64 must be 0 or 1");
   if (m->n_nodes > 0 && (!m->coords || !m->row_ptr)) return fail(FTLE_EINVAL, "mesh pointers are NULL");
   if (m->nnz > 0 && !m->col_idx) return fail(FTLE_EINVAL, "col_idx is NULL");
+  if (m->ell_width < 0 || m->reserved != 0) return fail(FTLE_EINVAL, "ell_width < 0 or reserved != 0");
+  if (m->ell_width > 0 && m->n_nodes > 0 && !m->ell_idx) return fail(FTLE_EINVAL, "ell_width set without ell_idx");
   return FTLE_OK;
 }
 
@@ -199,6 +202,10 @@ GradArgs make_grad_args(const ftle_mesh* m, const void* phi, double T, void* ftl
   g.coords = m->coords;
   g.row_ptr = m->row_ptr;
   g.col_idx = m->col_idx;
+  if (m->ell_width > 0 && m->ell_idx) {
+    g.ell = m->ell_idx;
+    g.ell_width = m->ell_width;
+  }
   g.phi = phi;
   g.ftle_out = ftle_out;
   g.lam_out = lam_out;
@@ -437,6 +444,27 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
   if (n_nodes > 0) FTLE_CUDA_CHECK(cudaMemcpyAsync(ftle_host, ftle_dev, ob, cudaMemcpyDeviceToHost, s));
   FTLE_CUDA_CHECK(cudaStreamSynchronize(s));
   return FTLE_OK;
+}
+
+int ftle_ell_from_csr(const ftle_mesh* mesh, int32_t width, int32_t* ell_idx, void* stream) {
+  int rc;
+  if ((rc = check_mesh(mesh))) return rc;
+  if (width < 1 || width > 1024) return fail(FTLE_EINVAL, "width must be in [1, 1024]");
+  if (mesh->n_nodes == 0) return FTLE_OK;
+  if (!ell_idx) return fail(FTLE_EINVAL, "ell_idx is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int32_t> rp((size_t)mesh->n_nodes + 1);
+  FTLE_CUDA_CHECK(cudaMemcpyAsync(rp.data(), mesh->row_ptr, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost, s));
+  FTLE_CUDA_CHECK(cudaStreamSynchronize(s));
+  int maxdeg = 0;
+  for (int64_t i = 0; i < mesh->n_nodes; ++i) {
+    const int d = rp[i + 1] - rp[i];
+    if (d < 0) return fail(FTLE_EINVAL, "row_ptr decreases at row %lld", (long long)i);
+    maxdeg = d > maxdeg ? d : maxdeg;
+  }
+  if (maxdeg > width) return fail(FTLE_ERANGE, "a row has %d neighbours, more than width %d", maxdeg, width);
+  return launch_ell_from_csr(mesh->n_nodes, mesh->row_ptr, mesh->col_idx, width, ell_idx,
+                             grid_for(mesh->n_nodes, 256, 8), s);
 }
 
 int ftle_read_counters(const void* workspace, ftle_counters* out, void* stream) {

@@ -45,6 +45,31 @@ __global__ void __launch_bounds__(256) k_grad_f32(GradArgs a) {
   }
 }
 
+// Float kernel over the fixed-width neighbour list (W = 0: width read at run time).
+template <int DIM, int PL, typename CT, int W>
+__global__ void __launch_bounds__(256) k_grad_f32_ell(GradArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = a.n;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    bool flag = false;
+    if (i < n) {
+      if constexpr (W > 0)
+        flag = grad_node_f32_ell<DIM, PL, CT, W>(a, i);
+      else
+        flag = grad_node_f32_ell_any<DIM, PL, CT>(a, i);
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask) {
+      const int leader = __ffs(mask) - 1;
+      unsigned long long basepos = 0;
+      if (lane == leader) basepos = atomicAdd(&a.hdr->n_flagged, (unsigned long long)__popc(mask));
+      basepos = __shfl_sync(0xffffffffu, basepos, leader);
+      if (flag) a.flag_list[basepos + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- double kernel
 
 template <int DIM, int PL, typename CT, typename OT>
@@ -69,14 +94,49 @@ __global__ void k_refine_mark(GradArgs a, int32_t* mark_list, uint32_t* bitmap) 
   }
 }
 
+// ----------------------------------------------------------------------------- ELL from CSR
+
+__global__ void k_ell_from_csr(int64_t n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                               int width, int32_t* __restrict__ ell) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int rs = row_ptr[i], re = row_ptr[i + 1];
+    for (int s = 0; s < width; ++s) ell[(int64_t)s * n + i] = (rs + s < re) ? col_idx[rs + s] : -1;
+  }
+}
+
+int launch_ell_from_csr(int64_t n, const int32_t* row_ptr, const int32_t* col_idx, int width, int32_t* ell, int grid,
+                        cudaStream_t s) {
+  k_ell_from_csr<<<grid, 256, 0, s>>>(n, row_ptr, col_idx, width, ell);
+  FTLE_LAUNCH_CHECK("k_ell_from_csr launch");
+  return FTLE_OK;
+}
+
 // ----------------------------------------------------------------------------- launchers
+
+template <int DIM, int PL, typename CT>
+static void grad_f32_ell_dispatch(const GradArgs& a, int grid, int block, cudaStream_t s) {
+  switch (a.ell_width) {
+    case 4: k_grad_f32_ell<DIM, PL, CT, 4><<<grid, block, 0, s>>>(a); break;
+    case 6: k_grad_f32_ell<DIM, PL, CT, 6><<<grid, block, 0, s>>>(a); break;
+    case 8: k_grad_f32_ell<DIM, PL, CT, 8><<<grid, block, 0, s>>>(a); break;
+    case 14: k_grad_f32_ell<DIM, PL, CT, 14><<<grid, block, 0, s>>>(a); break;
+    case 16: k_grad_f32_ell<DIM, PL, CT, 16><<<grid, block, 0, s>>>(a); break;
+    default: k_grad_f32_ell<DIM, PL, CT, 0><<<grid, block, 0, s>>>(a); break;
+  }
+}
 
 template <int DIM, int PL>
 static void grad_f32_dispatch(bool coord64, const GradArgs& a, int grid, int block, cudaStream_t s) {
-  if (coord64)
+  if (a.ell) {
+    if (coord64)
+      grad_f32_ell_dispatch<DIM, PL, double>(a, grid, block, s);
+    else
+      grad_f32_ell_dispatch<DIM, PL, float>(a, grid, block, s);
+  } else if (coord64) {
     k_grad_f32<DIM, PL, double><<<grid, block, 0, s>>>(a);
-  else
+  } else {
     k_grad_f32<DIM, PL, float><<<grid, block, 0, s>>>(a);
+  }
 }
 
 int launch_grad_f32(int dim, int phi_layout, bool coord64, const GradArgs& a, int grid, int block,

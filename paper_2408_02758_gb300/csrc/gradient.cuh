@@ -23,6 +23,8 @@ struct GradArgs {
   float refine_kappa;          // float kernel: flag nodes with ln(lambda_max) * h_i < refine_kappa
   ftle_counters* hdr;
   int32_t* flag_list;          // float kernel appends here
+  const int32_t* ell;          // nullable: fixed-width neighbour list [ell_width][n], -1 = none
+  int ell_width;
   const int32_t* list;         // double kernel: nullable node list ...
   const unsigned long long* list_count;  // ... and its device-side length
 };
@@ -37,6 +39,8 @@ int launch_grad_f32(int dim, int phi_layout, bool coord64, const GradArgs& a, in
                     cudaStream_t stream);
 int launch_grad_f64(int dim, int phi_layout, bool coord64, bool out64, const GradArgs& a, int grid,
                     int block, cudaStream_t stream);
+int launch_ell_from_csr(int64_t n, const int32_t* row_ptr, const int32_t* col_idx, int width, int32_t* ell, int grid,
+                        cudaStream_t s);
 int launch_refine_mark(const GradArgs& a, int32_t* mark_list, uint32_t* bitmap, int grid, int block,
                        cudaStream_t stream);
 

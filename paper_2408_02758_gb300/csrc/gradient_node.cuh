@@ -56,48 +56,51 @@ __device__ __forceinline__ T sym3_lmax(T a00, T a01, T a02, T a11, T a12, T a22,
   return q + T(2) * p * cos(acos(r) / T(3));
 }
 
-// One node of the float kernel: writes FTLE (NaN when flagged) and lambda_max, returns whether
-// the node needs the FP64 path.
+// Float moments of one neighbour: M += dx dx^T (upper triangle), B += dphi dx^T.
 template <int DIM, int PL, typename CT>
-__device__ __forceinline__ bool grad_node_f32(const GradArgs& a, int64_t i) {
+__device__ __forceinline__ void grad_accumulate(const GradArgs& a, int64_t j, const CT* xi, const float2* pi,
+                                                float* m, float* b) {
   const int64_t n = a.n;
-  bool flag = false;
-  const int rs = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
-  CT xi[DIM];
-  float2 pi[DIM];
+  float dx[DIM], dp[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    dx[d] = (float)(ldc<CT>(a.coords, d * n + j) - xi[d]);
+    const float2 pj = ld_phi32<PL>(a.phi, d * n + j);
+    dp[d] = (pj.x - pi[d].x) + (pj.y - pi[d].y);
+  }
+  int q = 0;
+#pragma unroll
+  for (int r = 0; r < DIM; ++r)
+#pragma unroll
+    for (int c = r; c < DIM; ++c, ++q) m[q] = fmaf(dx[r], dx[c], m[q]);
+#pragma unroll
+  for (int r = 0; r < DIM; ++r)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) b[r * DIM + c] = fmaf(dp[r], dx[c], b[r * DIM + c]);
+}
+
+template <int DIM, int PL, typename CT>
+__device__ __forceinline__ void grad_load_self(const GradArgs& a, int64_t i, CT* xi, float2* pi, float* m, float* b) {
+  const int64_t n = a.n;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     xi[d] = ldc<CT>(a.coords, d * n + i);
     pi[d] = ld_phi32<PL>(a.phi, d * n + i);
   }
-  constexpr int NM = DIM * (DIM + 1) / 2;
-  float m[NM], b[DIM * DIM];
 #pragma unroll
-  for (int q = 0; q < NM; ++q) m[q] = 0.f;
+  for (int q = 0; q < DIM * (DIM + 1) / 2; ++q) m[q] = 0.f;
 #pragma unroll
   for (int q = 0; q < DIM * DIM; ++q) b[q] = 0.f;
-  for (int e = rs; e < re; ++e) {
-    const int j = __ldg(a.col_idx + e);
-    float dx[DIM], dp[DIM];
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      dx[d] = (float)(ldc<CT>(a.coords, d * n + j) - xi[d]);
-      const float2 pj = ld_phi32<PL>(a.phi, d * n + j);
-      dp[d] = (pj.x - pi[d].x) + (pj.y - pi[d].y);
-    }
-    int q = 0;
-#pragma unroll
-    for (int r = 0; r < DIM; ++r)
-#pragma unroll
-      for (int c = r; c < DIM; ++c, ++q) m[q] = fmaf(dx[r], dx[c], m[q]);
-#pragma unroll
-    for (int r = 0; r < DIM; ++r)
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) b[r * DIM + c] = fmaf(dp[r], dx[c], b[r * DIM + c]);
-  }
+}
+
+// From the float moments of k neighbours: F, C = F^T F, lambda_max, FTLE (NaN when flagged) and
+// lambda_max to the outputs; returns whether the node needs the FP64 path.
+template <int DIM>
+__device__ __forceinline__ bool grad_finish_f32(const GradArgs& a, int64_t i, int k, const float* m, const float* b) {
+  bool flag = false;
   float lam = NAN, mu = NAN;
   const float trm = DIM == 2 ? m[0] + m[2] : m[0] + m[3] + m[5];
-  if (re - rs < DIM) {
+  if (k < DIM) {
     flag = true;
   } else if constexpr (DIM == 2) {
     const float det = m[0] * m[2] - m[1] * m[1];
@@ -145,13 +148,68 @@ __device__ __forceinline__ bool grad_node_f32(const GradArgs& a, int64_t i) {
     }
   }
   mu = lam - 1.0f;
-  const float h_i = sqrtf(trm / (float)(re - rs > 0 ? re - rs : 1));
+  const float h_i = sqrtf(trm / (float)(k > 0 ? k : 1));
   const bool sensitive = (a.refine_kappa >= 0.f) && !(log1pf(mu) * h_i >= a.refine_kappa);
   flag = flag || !(mu >= kMuFloor) || sensitive || !(lam == lam);
   const float ftle = flag ? NAN : log1pf(mu) * (float)a.inv_2absT;
   reinterpret_cast<float*>(a.ftle_out)[i] = ftle;
   if (a.lam_out) a.lam_out[i] = flag ? NAN : (double)lam;
   return flag;
+}
+
+// One node of the float kernel over its CSR row.
+template <int DIM, int PL, typename CT>
+__device__ __forceinline__ bool grad_node_f32(const GradArgs& a, int64_t i) {
+  const int rs = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+  CT xi[DIM];
+  float2 pi[DIM];
+  float m[DIM * (DIM + 1) / 2], b[DIM * DIM];
+  grad_load_self<DIM, PL, CT>(a, i, xi, pi, m, b);
+  for (int e = rs; e < re; ++e) grad_accumulate<DIM, PL, CT>(a, __ldg(a.col_idx + e), xi, pi, m, b);
+  return grad_finish_f32<DIM>(a, i, re - rs, m, b);
+}
+
+// One node over the fixed-width neighbour list of the paper's decoupled layout (Section 2.2):
+// W slots stored slot-major (ell[s * n + i]), -1 marking an absent neighbour.  All W indices are
+// independent coalesced loads, and the unrolled gathers can all be in flight at once.
+template <int DIM, int PL, typename CT, int W>
+__device__ __forceinline__ bool grad_node_f32_ell(const GradArgs& a, int64_t i) {
+  const int64_t n = a.n;
+  int js[W];
+#pragma unroll
+  for (int s = 0; s < W; ++s) js[s] = __ldg(a.ell + (int64_t)s * n + i);
+  CT xi[DIM];
+  float2 pi[DIM];
+  float m[DIM * (DIM + 1) / 2], b[DIM * DIM];
+  grad_load_self<DIM, PL, CT>(a, i, xi, pi, m, b);
+  int k = 0;
+#pragma unroll
+  for (int s = 0; s < W; ++s) {
+    if (js[s] >= 0) {
+      grad_accumulate<DIM, PL, CT>(a, js[s], xi, pi, m, b);
+      ++k;
+    }
+  }
+  return grad_finish_f32<DIM>(a, i, k, m, b);
+}
+
+// Fixed-width list of a width without its own instantiation.
+template <int DIM, int PL, typename CT>
+__device__ __forceinline__ bool grad_node_f32_ell_any(const GradArgs& a, int64_t i) {
+  const int64_t n = a.n;
+  CT xi[DIM];
+  float2 pi[DIM];
+  float m[DIM * (DIM + 1) / 2], b[DIM * DIM];
+  grad_load_self<DIM, PL, CT>(a, i, xi, pi, m, b);
+  int k = 0;
+  for (int s = 0; s < a.ell_width; ++s) {
+    const int j = __ldg(a.ell + (int64_t)s * n + i);
+    if (j >= 0) {
+      grad_accumulate<DIM, PL, CT>(a, j, xi, pi, m, b);
+      ++k;
+    }
+  }
+  return grad_finish_f32<DIM>(a, i, k, m, b);
 }
 
 // One node in double: the least-squares fit, mu = lambda_max(F^T F - I), FTLE; counts and NaNs

@@ -26,7 +26,8 @@ FTLE_OK, FTLE_EINVAL, FTLE_ECUDA, FTLE_EWORKSPACE, FTLE_EUNSUPPORTED, FTLE_ERANG
 
 class ftle_mesh(Structure):
     _fields_ = [("dim", c_int32), ("coord_fp64", c_int32), ("n_nodes", c_int64), ("nnz", c_int64),
-                ("coords", c_void_p), ("row_ptr", c_void_p), ("col_idx", c_void_p)]
+                ("coords", c_void_p), ("row_ptr", c_void_p), ("col_idx", c_void_p), ("ell_width", c_int32),
+                ("reserved", c_int32), ("ell_idx", c_void_p)]
 
 
 class ftle_flow(Structure):
@@ -72,6 +73,7 @@ _SIGS = [
                                   c_double, c_double, c_double, c_int32, c_void_p, c_void_p, c_size_t,
                                   POINTER(ftle_options), c_void_p]),
     ("ftle_read_counters", c_int, [c_void_p, POINTER(ftle_counters), c_void_p]),
+    ("ftle_ell_from_csr", c_int, [POINTER(ftle_mesh), c_int32, c_void_p, c_void_p]),
     ("ftle_gradient_eig_noalloc", c_int, [POINTER(ftle_mesh), c_void_p, c_int32, c_double, c_void_p, c_void_p,
                                           POINTER(ftle_options), c_void_p]),
     ("ftle_batch_workspace_bytes", c_size_t, [c_int32, POINTER(ftle_mesh), c_int32]),
@@ -186,6 +188,25 @@ class DeviceMesh:
 
         return DeviceMesh(torch.from_numpy(np.ascontiguousarray(mesh.coords)).to(device),
                           torch.from_numpy(mesh.row_ptr).to(device), torch.from_numpy(mesh.col_idx).to(device))
+
+    def attach_ell(self, width: int | None = None, stream=None):
+        """Build the fixed-width (-1 padded) neighbour list on the device and let the float gradient
+        kernel use it.  width defaults to the largest row length."""
+        import torch
+
+        if width is None:
+            width = int((self.row_ptr[1:] - self.row_ptr[:-1]).max().item()) if self.n_nodes else 1
+        self.ell = torch.empty((width, self.n_nodes), dtype=torch.int32, device=self.coords.device)
+        _check("ftle_ell_from_csr", lib().ftle_ell_from_csr(ctypes.byref(self.desc), width, _ptr(self.ell),
+                                                            _stream(stream)))
+        self.desc.ell_width = width
+        self.desc.ell_idx = _ptr(self.ell)
+        return self
+
+    def detach_ell(self):
+        self.desc.ell_width = 0
+        self.desc.ell_idx = None
+        return self
 
     @property
     def dim(self) -> int:

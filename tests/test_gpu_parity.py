@@ -270,3 +270,31 @@ def test_float_float_readvection_matches_fp64_flowmap(F):
     err = np.abs(ph[:, marked] - ref).max()
     assert err < 1e-10, err
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("preset,scale,width", [(1, 1 / 16, None), (1, 1 / 16, 7), (2, 1 / 8, None), (0, 1 / 4, 4)])
+def test_fixed_width_neighbour_list_matches_csr(F, preset, scale, width):
+    """The paper's fixed-width, -1 padded neighbour list gives bit-identical FTLE to the CSR rows
+    (same neighbour order, same arithmetic); width 7 exercises the run-time-width kernel."""
+    import torch
+
+    w = I.preset(preset, scale=scale)
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    a = F.compute(dm, w.flow, w.T, w.dt, w.precision).cpu()
+    dm.attach_ell(width)
+    assert dm.desc.ell_width == (width or int(np.diff(w.mesh.row_ptr).max()))
+    ell = dm.ell.cpu().numpy()
+    rp, ci = w.mesh.row_ptr, w.mesh.col_idx
+    for i in (0, 1, w.mesh.n_nodes // 2, w.mesh.n_nodes - 1):
+        row = ci[rp[i]:rp[i + 1]]
+        assert np.array_equal(ell[: len(row), i], row) and np.all(ell[len(row):, i] == -1)
+    b = F.compute(dm, w.flow, w.T, w.dt, w.precision).cpu()
+    assert torch.equal(torch.isnan(a), torch.isnan(b)) and torch.equal(a[~torch.isnan(a)], b[~torch.isnan(b)])
+
+
+def test_fixed_width_list_rejects_long_rows(F):
+    w = I.preset(2, scale=1 / 32)
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    with pytest.raises(F.FTLEError) as e:
+        dm.attach_ell(8)  # Kuhn rows have 14 neighbours
+    assert e.value.status == F.FTLE_ERANGE
