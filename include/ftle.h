@@ -131,8 +131,14 @@ typedef struct ftle_options {
 
 /* ---------------------------------------------------------------------------------- sizes */
 
-/* Bytes of a flowmap buffer for `precision` (0 on bad arguments). */
+/* Bytes of a flowmap buffer for `precision` (0 on bad arguments).  For FP32C the buffer holds the
+ * (hi, lo) pairs float2 [dim][n] followed, at the next 256-byte boundary, by one 32-byte record
+ * per node that the float gradient kernel reads (coordinates, hi parts and low parts packed:
+ * 2D {x, y, hx, hy}{lx, ly, 0, 0}; 3D {x, y, z, hx}{hy, hz, lx, bf16(ly) | bf16(lz) << 16}). */
 size_t ftle_flowmap_bytes(int32_t dim, int64_t n_nodes, int32_t precision);
+
+/* Bytes of one checkpoint slot: the state alone (the FP32C (hi, lo) pairs, without records). */
+size_t ftle_checkpoint_bytes(int32_t dim, int64_t n_nodes, int32_t precision);
 
 /* Bytes of the workspace ftle_gradient_eig / ftle_refine / ftle_compute need for n_nodes:
  * counters header, the FP64-path node list and the re-advection mark set.  The workspace must
@@ -144,8 +150,8 @@ size_t ftle_workspace_bytes(int64_t n_nodes);
 /* Flowmap by RK4 (the input of the FTLE core, Section 2.2).
  *   flowmap     device out, ftle_flowmap_bytes(dim, n, precision) bytes, layout per precision.
  *   checkpoints nullable device out: the state every ckpt_every steps for the adjoint
- *               (ftle_backward); ckpt_count = n_steps / ckpt_every + 1 slots of one
- *               flowmap each (slot s holds the state after s * ckpt_every steps).
+ *               (ftle_backward); ckpt_count = n_steps / ckpt_every + 1 slots of
+ *               ftle_checkpoint_bytes each (slot s holds the state after s * ckpt_every steps).
  *   ckpt_every  > 0 when checkpoints is given, else ignored.
  * Errors: FTLE_EINVAL (null mesh/flow/flowmap, dt = 0, T = 0, flow kind not valid for dim,
  * coords precision not matching FP64 mode's need), FTLE_ERANGE (more than 2^31 - 1 steps). */

@@ -352,7 +352,7 @@ int ftle_backward(const ftle_mesh* mesh, const ftle_flow* flow, double t0, doubl
   AdvArgs a = make_adv_args(mesh, flow, t0, T, dt, nsteps);
   a.ckpt = const_cast<void*>(checkpoints);
   a.ckpt_every = ckpt_every;
-  a.ckpt_stride_bytes = (int64_t)ftle_flowmap_bytes(mesh->dim, mesh->n_nodes, precision);
+  a.ckpt_stride_bytes = (int64_t)ftle_checkpoint_bytes(mesh->dim, mesh->n_nodes, precision);
   const size_t smem = sizeof(float4) * (size_t)(2 * ckpt_every + 1) + sizeof(float2) * (size_t)ckpt_every * kAdjBlock;
   if (precision == FTLE_PREC_FP32C)
     rc = launch_adjoint_rk4<P32C, O32PAIR>(a, phibar, partial, W.nblocks, smem, s);

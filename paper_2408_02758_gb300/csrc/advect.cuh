@@ -28,6 +28,7 @@ struct AdvArgs {
   const int32_t* list;         // nullable: process list[0 .. *list_count)
   const unsigned long long* list_count;
   int lanes;                   // active threads per block (0 = all): few-node lists spread wider
+  float4* rec;                 // nullable: gradient records of a compensated flowmap
 };
 
 // ------------------------------------------------------------------------- velocity dispatch
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
     const bool active = (int)threadIdx.x < lanes && slot < count;
     const int64_t i = active ? (a.list ? (int64_t)a.list[slot] : slot) : 0;
 
-    float xh[DIM], xl[DIM];
+    float xh[DIM], xl[DIM], x0[DIM];
     double xd[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -291,6 +292,7 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
       xd[d] = c;
       xh[d] = (float)c;
       xl[d] = (float)(c - (double)xh[d]);
+      x0[d] = xh[d];
     }
     if (a.ckpt && active) store_state<OUT, DIM>(a.ckpt, a.n_mesh, i, xh, xl, xd);
     int ck_left = a.ckpt_every;
@@ -328,6 +330,9 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
     if (active) {
       split_state<PREC, DIM>(xh, xl, xd);
       store_state<OUT, DIM>(a.out, a.n_mesh, i, xh, xl, xd);
+      if constexpr (OUT == O32PAIR) {
+        if (a.rec) store_record<DIM>(a.rec, i, x0, xh, xl);
+      }
     }
   }
 }

@@ -79,9 +79,12 @@ __global__ void __launch_bounds__(32) k_advect_ds(AdvArgs a) {
     const bool active = (int)threadIdx.x < lanes && slot < count;
     const int64_t i = active ? (a.list ? (int64_t)a.list[slot] : slot) : 0;
     dsf x[DIM];
+    float x0[DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d)
+    for (int d = 0; d < DIM; ++d) {
       x[d] = ds_from_double(active ? (double)__ldg(reinterpret_cast<const CT*>(a.coords) + d * a.n_mesh + i) : 0.0);
+      x0[d] = x[d].h;
+    }
 
     for (int ch = 0; ch < nchunks; ++ch) {
       const int k0 = ch * kAdvChunk;
@@ -122,8 +125,14 @@ __global__ void __launch_bounds__(32) k_advect_ds(AdvArgs a) {
     }
     if (active) {
       float2* o = reinterpret_cast<float2*>(a.out);
+      float ph[DIM], pl[DIM];
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) o[d * a.n_mesh + i] = make_float2(x[d].h, x[d].l);
+      for (int d = 0; d < DIM; ++d) {
+        o[d * a.n_mesh + i] = make_float2(x[d].h, x[d].l);
+        ph[d] = x[d].h;
+        pl[d] = x[d].l;
+      }
+      if (a.rec) store_record<DIM>(a.rec, i, x0, ph, pl);
     }
   }
 }
@@ -159,8 +168,12 @@ __global__ void __launch_bounds__(32) k_batch_advect_ds(const BatchInst* __restr
       }
     };
     dsf x[DIM];
+    float x0[DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) x[d] = ds_from_double((double)__ldg(reinterpret_cast<const float*>(a.coords) + d * a.n_mesh + i));
+    for (int d = 0; d < DIM; ++d) {
+      x[d] = ds_from_double((double)__ldg(reinterpret_cast<const float*>(a.coords) + d * a.n_mesh + i));
+      x0[d] = x[d].h;
+    }
     dsf c2 = coef(0);
     for (int k = 0; k < a.nsteps; ++k) {
       const dsf c0 = c2, c1 = coef(2 * k + 1);
@@ -181,8 +194,14 @@ __global__ void __launch_bounds__(32) k_batch_advect_ds(const BatchInst* __restr
       }
     }
     float2* o = reinterpret_cast<float2*>(a.out);
+    float ph[DIM], pl[DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) o[d * a.n_mesh + i] = make_float2(x[d].h, x[d].l);
+    for (int d = 0; d < DIM; ++d) {
+      o[d * a.n_mesh + i] = make_float2(x[d].h, x[d].l);
+      ph[d] = x[d].h;
+      pl[d] = x[d].l;
+    }
+    if (a.rec) store_record<DIM>(a.rec, i, x0, ph, pl);
   }
 }
 

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_batch_advect(const BatchInst* __restric
     const AdvArgs a = insts[item.inst].adv;
     const int64_t i = (int64_t)item.lo + threadIdx.x;
     const bool active = i < item.hi;
-    float xh[DIM], xl[DIM];
+    float xh[DIM], xl[DIM], x0[DIM];
     double xd[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(256) k_batch_advect(const BatchInst* __restric
       xd[d] = c;
       xh[d] = (float)c;
       xl[d] = 0.f;
+      x0[d] = xh[d];
     }
     const int nchunks = (a.nsteps + kAdvChunk - 1) / kAdvChunk;
     for (int ch = 0; ch < nchunks; ++ch) {
@@ -74,6 +75,9 @@ __global__ void __launch_bounds__(256) k_batch_advect(const BatchInst* __restric
     if (active) {
       split_state<PREC, DIM>(xh, xl, xd);
       store_state<OUT, DIM>(a.out, a.n_mesh, i, xh, xl, xd);
+      if constexpr (OUT == O32PAIR) {
+        if (a.rec) store_record<DIM>(a.rec, i, x0, xh, xl);
+      }
     }
   }
 }
@@ -94,7 +98,13 @@ __global__ void __launch_bounds__(256) k_batch_grad(const BatchInst* __restrict_
     const GradArgs g = insts[item.inst].grad;
     for (int base = item.lo; base < item.hi; base += blockDim.x) {
       const int i = base + threadIdx.x;
-      const bool flag = (i < item.hi) ? grad_node_f32<DIM, PL, float>(g, i) : false;
+      bool flag = false;
+      if (i < item.hi) {
+        if constexpr (PL == PHI32PAIR)
+          flag = grad_node_f32_rec<DIM>(g, i);
+        else
+          flag = grad_node_f32<DIM, PL, float>(g, i);
+      }
       const unsigned mask = __ballot_sync(0xffffffffu, flag);
       if (mask) {
         const int leader = __ffs(mask) - 1;
@@ -291,8 +301,13 @@ int plan_batch(int32_t n_inst, const ftle_mesh* meshes, const ftle_flow* flows, 
     void* phi = P.ws + P.L.phi_off[q];
     bi.adv = make_adv_args(&meshes[q], &flows[q], 0.0, T[q], dt, nsteps);
     bi.adv.out = phi;
+    float4* rec = precision == FTLE_PREC_FP32C
+                      ? reinterpret_cast<float4*>(reinterpret_cast<char*>(phi) + rec_offset(meshes[q].dim, meshes[q].n_nodes))
+                      : nullptr;
+    bi.adv.rec = rec;
     Launch Lq = Lc;
     bi.grad = make_grad_args(&meshes[q], phi, T[q], ftle_out[q], nullptr, workspace, Lq);
+    bi.grad.rec = rec;
     bi.grad.hdr = hdr;        // batch-wide counters
     bi.grad.flag_list = nullptr;
     bi.off = off;

@@ -221,10 +221,16 @@ int phi_layout_of(int precision) {
 }
 
 // One call of the gradient stage (float kernel + FP64 fix-up, or the FP64 kernel).
+float4* rec_ptr(const ftle_mesh* m, const void* phi, int precision) {
+  if (precision != FTLE_PREC_FP32C) return nullptr;
+  return reinterpret_cast<float4*>(reinterpret_cast<char*>(const_cast<void*>(phi)) + rec_offset(m->dim, m->n_nodes));
+}
+
 int run_gradient(const ftle_mesh* m, const void* phi, int precision, double T, void* ftle_out,
                  double* lam_out, void* ws, const Launch& L, cudaStream_t s) {
   if (m->n_nodes == 0) return FTLE_OK;
   GradArgs g = make_grad_args(m, phi, T, ftle_out, lam_out, ws, L);
+  g.rec = rec_ptr(m, phi, precision);
   const int sms = device_sm_count() > 0 ? device_sm_count() : 1;
   const bool c64 = m->coord_fp64 != 0;
   if (precision == FTLE_PREC_FP64) {
@@ -262,6 +268,7 @@ int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
   a.list = mark;
   a.list_count = &hdr->n_readvected;
   a.lanes = L.refine_lanes;
+  a.rec = rec_ptr(m, phi, precision);
   rc = launch_advect_ds(fl->kind, m->dim, m->coord_fp64 != 0, a, sms * 8, 32, s);
   if (rc) return rc;
   return launch_grad_f64(m->dim, PHI32PAIR, m->coord_fp64 != 0, false, g, sms * 4, 128, s);
@@ -274,7 +281,8 @@ int run_advect(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
   a.out = phi;
   a.ckpt = ckpt;
   a.ckpt_every = ckpt ? ckpt_every : 0;
-  a.ckpt_stride_bytes = (int64_t)ftle_flowmap_bytes(m->dim, m->n_nodes, precision);
+  a.ckpt_stride_bytes = (int64_t)ftle_checkpoint_bytes(m->dim, m->n_nodes, precision);
+  a.rec = rec_ptr(m, phi, precision);
   const int prec = precision == FTLE_PREC_FP64 ? P64 : (precision == FTLE_PREC_FP32 ? P32 : P32C);
   const int out = precision == FTLE_PREC_FP64 ? O64 : (precision == FTLE_PREC_FP32 ? O32 : O32PAIR);
   int block = L.advect_block;
@@ -308,13 +316,19 @@ const char* ftle_status_string(int status) {
   }
 }
 
-size_t ftle_flowmap_bytes(int32_t dim, int64_t n_nodes, int32_t precision) {
+size_t ftle_checkpoint_bytes(int32_t dim, int64_t n_nodes, int32_t precision) {
   if ((dim != 2 && dim != 3) || n_nodes < 0) return 0;
   const size_t per = precision == FTLE_PREC_FP32 ? sizeof(float) : (precision == FTLE_PREC_FP64 ||
                                                                        precision == FTLE_PREC_FP32C)
                                                                           ? 8
                                                                           : 0;
   return per * (size_t)dim * (size_t)n_nodes;
+}
+
+size_t ftle_flowmap_bytes(int32_t dim, int64_t n_nodes, int32_t precision) {
+  if ((dim != 2 && dim != 3) || n_nodes < 0) return 0;
+  if (precision == FTLE_PREC_FP32C) return rec_offset(dim, n_nodes) + 32 * (size_t)n_nodes;
+  return ftle_checkpoint_bytes(dim, n_nodes, precision);
 }
 
 size_t ftle_workspace_bytes(int64_t n_nodes) {

@@ -39,6 +39,7 @@ GradArgs make_grad_args(const ftle_mesh* m, const void* phi, double T, void* ftl
                         void* ws, const Launch& L);
 int run_advect(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, double dt, int nsteps,
                int precision, void* phi, void* ckpt, int ckpt_every, const Launch& L, cudaStream_t s);
+float4* rec_ptr(const ftle_mesh* m, const void* phi, int precision);
 int run_gradient(const ftle_mesh* m, const void* phi, int precision, double T, void* ftle_out,
                  double* lam_out, void* ws, const Launch& L, cudaStream_t s);
 int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, double dt, int nsteps,

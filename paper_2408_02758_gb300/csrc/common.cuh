@@ -107,6 +107,49 @@ __device__ __forceinline__ void fsincos_c(float xh, float xl, float& s, float& c
 
 __device__ __forceinline__ void fsincos(float x, float& s, float& c) { fsincos_c(x, 0.0f, s, c); }
 
+// ------------------------------------------------------------------------- gradient records
+
+// A compensated flowmap carries, after its (hi, lo) pairs, one 32-byte record per node for the
+// float gradient kernel, so that a neighbour costs one address and two 16-byte loads:
+//   2D: {x, y, phx_h, phy_h} {phx_l, phy_l, 0, 0}
+//   3D: {x, y, z, phx_h} {phy_h, phz_h, phx_l, bf16(phy_l) | bf16(phz_l) << 16}
+// (x the node's float coordinates).  The 3D record keeps two low parts in bfloat16: 8
+// significant bits of a part below half an ulp of its high part, i.e. ~2^-33 relative to the
+// position.  The full (hi, lo) pairs stay in the flowmap for the FP64 paths.
+__host__ __device__ inline size_t rec_offset(int dim, int64_t n) {
+  return ((size_t)8 * (size_t)dim * (size_t)n + 255) & ~size_t(255);
+}
+
+__device__ __forceinline__ uint32_t bf16_bits(float v) {  // round to nearest even
+  const uint32_t u = __float_as_uint(v);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+
+template <int DIM>
+__device__ __forceinline__ void store_record(float4* rec, int64_t i, const float* x, const float* ph, const float* pl) {
+  if constexpr (DIM == 2) {
+    rec[2 * i] = make_float4(x[0], x[1], ph[0], ph[1]);
+    rec[2 * i + 1] = make_float4(pl[0], pl[1], 0.f, 0.f);
+  } else {
+    rec[2 * i] = make_float4(x[0], x[1], x[2], ph[0]);
+    const uint32_t w = bf16_bits(pl[1]) | (bf16_bits(pl[2]) << 16);
+    rec[2 * i + 1] = make_float4(ph[1], ph[2], pl[0], __uint_as_float(w));
+  }
+}
+
+template <int DIM>
+__device__ __forceinline__ void load_record(const float4* rec, int64_t i, float* x, float* ph, float* pl) {
+  const float4 a = __ldg(rec + 2 * i), b = __ldg(rec + 2 * i + 1);
+  if constexpr (DIM == 2) {
+    x[0] = a.x; x[1] = a.y; ph[0] = a.z; ph[1] = a.w; pl[0] = b.x; pl[1] = b.y;
+  } else {
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; ph[0] = a.w; ph[1] = b.x; ph[2] = b.y; pl[0] = b.z;
+    const uint32_t w = __float_as_uint(b.w);
+    pl[1] = __uint_as_float(w << 16);
+    pl[2] = __uint_as_float(w & 0xFFFF0000u);
+  }
+}
+
 // ------------------------------------------------------------------------------ flow params
 
 constexpr double kPi = 3.14159265358979323846;

@@ -26,13 +26,19 @@ namespace ftle {
 
 // ----------------------------------------------------------------------------- float kernel
 
-template <int DIM, int PL, typename CT>
+template <int DIM, int PL, typename CT, bool REC>
 __global__ void __launch_bounds__(256) k_grad_f32(GradArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t n = a.n;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
-    const bool flag = (i < n) ? grad_node_f32<DIM, PL, CT>(a, i) : false;
+    bool flag = false;
+    if (i < n) {
+      if constexpr (REC)
+        flag = grad_node_f32_rec<DIM>(a, i);
+      else
+        flag = grad_node_f32<DIM, PL, CT>(a, i);
+    }
     // warp-aggregated append of flagged nodes (the loop is uniform per block)
     const unsigned mask = __ballot_sync(0xffffffffu, flag);
     if (mask) {
@@ -46,7 +52,7 @@ __global__ void __launch_bounds__(256) k_grad_f32(GradArgs a) {
 }
 
 // Float kernel over the fixed-width neighbour list (W = 0: width read at run time).
-template <int DIM, int PL, typename CT, int W>
+template <int DIM, int PL, typename CT, int W, bool REC>
 __global__ void __launch_bounds__(256) k_grad_f32_ell(GradArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t n = a.n;
@@ -54,7 +60,9 @@ __global__ void __launch_bounds__(256) k_grad_f32_ell(GradArgs a) {
     const int64_t i = base + threadIdx.x;
     bool flag = false;
     if (i < n) {
-      if constexpr (W > 0)
+      if constexpr (REC)
+        flag = grad_node_f32_ell_rec<DIM, W>(a, i);
+      else if constexpr (W > 0)
         flag = grad_node_f32_ell<DIM, PL, CT, W>(a, i);
       else
         flag = grad_node_f32_ell_any<DIM, PL, CT>(a, i);
@@ -113,29 +121,35 @@ int launch_ell_from_csr(int64_t n, const int32_t* row_ptr, const int32_t* col_id
 
 // ----------------------------------------------------------------------------- launchers
 
-template <int DIM, int PL, typename CT>
+template <int DIM, int PL, typename CT, bool REC>
 static void grad_f32_ell_dispatch(const GradArgs& a, int grid, int block, cudaStream_t s) {
   switch (a.ell_width) {
-    case 4: k_grad_f32_ell<DIM, PL, CT, 4><<<grid, block, 0, s>>>(a); break;
-    case 6: k_grad_f32_ell<DIM, PL, CT, 6><<<grid, block, 0, s>>>(a); break;
-    case 8: k_grad_f32_ell<DIM, PL, CT, 8><<<grid, block, 0, s>>>(a); break;
-    case 14: k_grad_f32_ell<DIM, PL, CT, 14><<<grid, block, 0, s>>>(a); break;
-    case 16: k_grad_f32_ell<DIM, PL, CT, 16><<<grid, block, 0, s>>>(a); break;
-    default: k_grad_f32_ell<DIM, PL, CT, 0><<<grid, block, 0, s>>>(a); break;
+    case 4: k_grad_f32_ell<DIM, PL, CT, 4, REC><<<grid, block, 0, s>>>(a); break;
+    case 6: k_grad_f32_ell<DIM, PL, CT, 6, REC><<<grid, block, 0, s>>>(a); break;
+    case 8: k_grad_f32_ell<DIM, PL, CT, 8, REC><<<grid, block, 0, s>>>(a); break;
+    case 14: k_grad_f32_ell<DIM, PL, CT, 14, REC><<<grid, block, 0, s>>>(a); break;
+    case 16: k_grad_f32_ell<DIM, PL, CT, 16, REC><<<grid, block, 0, s>>>(a); break;
+    default: k_grad_f32_ell<DIM, PL, CT, 0, REC><<<grid, block, 0, s>>>(a); break;
   }
 }
 
 template <int DIM, int PL>
 static void grad_f32_dispatch(bool coord64, const GradArgs& a, int grid, int block, cudaStream_t s) {
+  // gradient records exist for compensated flowmaps; they carry float coordinates
+  const bool rec = PL == PHI32PAIR && a.rec && !coord64;
   if (a.ell) {
-    if (coord64)
-      grad_f32_ell_dispatch<DIM, PL, double>(a, grid, block, s);
+    if (rec)
+      grad_f32_ell_dispatch<DIM, PL, float, true>(a, grid, block, s);
+    else if (coord64)
+      grad_f32_ell_dispatch<DIM, PL, double, false>(a, grid, block, s);
     else
-      grad_f32_ell_dispatch<DIM, PL, float>(a, grid, block, s);
+      grad_f32_ell_dispatch<DIM, PL, float, false>(a, grid, block, s);
+  } else if (rec) {
+    k_grad_f32<DIM, PL, float, true><<<grid, block, 0, s>>>(a);
   } else if (coord64) {
-    k_grad_f32<DIM, PL, double><<<grid, block, 0, s>>>(a);
+    k_grad_f32<DIM, PL, double, false><<<grid, block, 0, s>>>(a);
   } else {
-    k_grad_f32<DIM, PL, float><<<grid, block, 0, s>>>(a);
+    k_grad_f32<DIM, PL, float, false><<<grid, block, 0, s>>>(a);
   }
 }
 

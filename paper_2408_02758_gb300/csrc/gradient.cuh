@@ -23,6 +23,7 @@ struct GradArgs {
   float refine_kappa;          // float kernel: flag nodes with ln(lambda_max) * h_i < refine_kappa
   ftle_counters* hdr;
   int32_t* flag_list;          // float kernel appends here
+  const float4* rec;           // nullable: gradient records of a compensated flowmap (float coords)
   const int32_t* ell;          // nullable: fixed-width neighbour list [ell_width][n], -1 = none
   int ell_width;
   const int32_t* list;         // double kernel: nullable node list ...

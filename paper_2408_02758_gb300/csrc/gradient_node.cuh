@@ -56,7 +56,21 @@ __device__ __forceinline__ T sym3_lmax(T a00, T a01, T a02, T a11, T a12, T a22,
   return q + T(2) * p * cos(acos(r) / T(3));
 }
 
-// Float moments of one neighbour: M += dx dx^T (upper triangle), B += dphi dx^T.
+// M += dx dx^T (upper triangle), B += dphi dx^T.
+template <int DIM>
+__device__ __forceinline__ void grad_moments(const float* dx, const float* dp, float* m, float* b) {
+  int q = 0;
+#pragma unroll
+  for (int r = 0; r < DIM; ++r)
+#pragma unroll
+    for (int c = r; c < DIM; ++c, ++q) m[q] = fmaf(dx[r], dx[c], m[q]);
+#pragma unroll
+  for (int r = 0; r < DIM; ++r)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) b[r * DIM + c] = fmaf(dp[r], dx[c], b[r * DIM + c]);
+}
+
+// Float moments of one neighbour j read from the coordinate and flowmap arrays.
 template <int DIM, int PL, typename CT>
 __device__ __forceinline__ void grad_accumulate(const GradArgs& a, int64_t j, const CT* xi, const float2* pi,
                                                 float* m, float* b) {
@@ -68,15 +82,21 @@ __device__ __forceinline__ void grad_accumulate(const GradArgs& a, int64_t j, co
     const float2 pj = ld_phi32<PL>(a.phi, d * n + j);
     dp[d] = (pj.x - pi[d].x) + (pj.y - pi[d].y);
   }
-  int q = 0;
+  grad_moments<DIM>(dx, dp, m, b);
+}
+
+// Float moments of one neighbour j read from its gradient record.
+template <int DIM>
+__device__ __forceinline__ void grad_accumulate_rec(const float4* rec, int64_t j, const float* xi, const float* hi,
+                                                    const float* li, float* m, float* b) {
+  float xj[DIM], hj[DIM], lj[DIM], dx[DIM], dp[DIM];
+  load_record<DIM>(rec, j, xj, hj, lj);
 #pragma unroll
-  for (int r = 0; r < DIM; ++r)
-#pragma unroll
-    for (int c = r; c < DIM; ++c, ++q) m[q] = fmaf(dx[r], dx[c], m[q]);
-#pragma unroll
-  for (int r = 0; r < DIM; ++r)
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) b[r * DIM + c] = fmaf(dp[r], dx[c], b[r * DIM + c]);
+  for (int d = 0; d < DIM; ++d) {
+    dx[d] = xj[d] - xi[d];
+    dp[d] = (hj[d] - hi[d]) + (lj[d] - li[d]);
+  }
+  grad_moments<DIM>(dx, dp, m, b);
 }
 
 template <int DIM, int PL, typename CT>
@@ -188,6 +208,50 @@ __device__ __forceinline__ bool grad_node_f32_ell(const GradArgs& a, int64_t i) 
     if (js[s] >= 0) {
       grad_accumulate<DIM, PL, CT>(a, js[s], xi, pi, m, b);
       ++k;
+    }
+  }
+  return grad_finish_f32<DIM>(a, i, k, m, b);
+}
+
+// Record-reading variants (compensated flowmaps with float coordinates): a neighbour is one
+// address and two 16-byte loads instead of 2 * DIM scattered loads.
+template <int DIM>
+__device__ __forceinline__ bool grad_node_f32_rec(const GradArgs& a, int64_t i) {
+  const int rs = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+  float xi[DIM], hi[DIM], li[DIM];
+  float m[DIM * (DIM + 1) / 2] = {}, b[DIM * DIM] = {};
+  load_record<DIM>(a.rec, i, xi, hi, li);
+  for (int e = rs; e < re; ++e) grad_accumulate_rec<DIM>(a.rec, __ldg(a.col_idx + e), xi, hi, li, m, b);
+  return grad_finish_f32<DIM>(a, i, re - rs, m, b);
+}
+
+template <int DIM, int W>
+__device__ __forceinline__ bool grad_node_f32_ell_rec(const GradArgs& a, int64_t i) {
+  const int64_t n = a.n;
+  int js[W > 0 ? W : 1];
+  if constexpr (W > 0) {
+#pragma unroll
+    for (int s = 0; s < W; ++s) js[s] = __ldg(a.ell + (int64_t)s * n + i);
+  }
+  float xi[DIM], hi[DIM], li[DIM];
+  float m[DIM * (DIM + 1) / 2] = {}, b[DIM * DIM] = {};
+  load_record<DIM>(a.rec, i, xi, hi, li);
+  int k = 0;
+  if constexpr (W > 0) {
+#pragma unroll
+    for (int s = 0; s < W; ++s) {
+      if (js[s] >= 0) {
+        grad_accumulate_rec<DIM>(a.rec, js[s], xi, hi, li, m, b);
+        ++k;
+      }
+    }
+  } else {
+    for (int s = 0; s < a.ell_width; ++s) {
+      const int j = __ldg(a.ell + (int64_t)s * n + i);
+      if (j >= 0) {
+        grad_accumulate_rec<DIM>(a.rec, j, xi, hi, li, m, b);
+        ++k;
+      }
     }
   }
   return grad_finish_f32<DIM>(a, i, k, m, b);

@@ -59,6 +59,7 @@ _SIGS = [
     ("ftle_last_error", c_char_p, []),
     ("ftle_status_string", c_char_p, [c_int]),
     ("ftle_flowmap_bytes", c_size_t, [c_int32, c_int64, c_int32]),
+    ("ftle_checkpoint_bytes", c_size_t, [c_int32, c_int64, c_int32]),
     ("ftle_workspace_bytes", c_size_t, [c_int64]),
     ("ftle_advect", c_int, [POINTER(ftle_mesh), POINTER(ftle_flow), c_double, c_double, c_double, c_int32,
                             c_void_p, c_void_p, c_int32, POINTER(ftle_options), c_void_p]),
@@ -307,8 +308,14 @@ def ftle_read_counters(workspace, stream=None) -> dict:
 # ------------------------------------------------------------------------------ buffer helpers
 
 
+def ftle_checkpoint_bytes(dim: int, n_nodes: int, precision) -> int:
+    return int(lib().ftle_checkpoint_bytes(dim, n_nodes, _prec(precision)))
+
+
 def flowmap_empty(dim: int, n_nodes: int, precision, device="cuda"):
-    """Uninitialised flowmap buffer in the layout of ``precision``."""
+    """Uninitialised flowmap buffer in the layout of ``precision``: (dim, n) float64 / float32, or
+    for fp32c a flat float32 buffer holding the (hi, lo) pairs and the gradient records (see
+    flowmap_pairs)."""
     import torch
 
     p = _prec(precision)
@@ -316,7 +323,12 @@ def flowmap_empty(dim: int, n_nodes: int, precision, device="cuda"):
         return torch.empty((dim, n_nodes), dtype=torch.float64, device=device)
     if p == PREC["fp32"]:
         return torch.empty((dim, n_nodes), dtype=torch.float32, device=device)
-    return torch.empty((dim, n_nodes, 2), dtype=torch.float32, device=device)
+    return torch.empty(ftle_flowmap_bytes(dim, n_nodes, p) // 4, dtype=torch.float32, device=device)
+
+
+def flowmap_pairs(phi, dim: int, n_nodes: int):
+    """(dim, n, 2) view of the (hi, lo) pairs at the start of an fp32c flowmap buffer."""
+    return phi[: dim * n_nodes * 2].view(dim, n_nodes, 2)
 
 
 def workspace_empty(nbytes: int, device="cuda"):
@@ -434,5 +446,6 @@ def checkpoints_empty(dim: int, n_nodes: int, n_steps: int, ckpt_every: int, pre
     import torch
 
     slots = n_steps // ckpt_every + 1
-    one = flowmap_empty(dim, n_nodes, precision, device=device)
-    return torch.empty((slots,) + tuple(one.shape), dtype=one.dtype, device=device)
+    nbytes = ftle_checkpoint_bytes(dim, n_nodes, precision)
+    dtype = torch.float64 if _prec(precision) == PREC["fp64"] else torch.float32
+    return torch.empty((slots, nbytes // dtype.itemsize), dtype=dtype, device=device)

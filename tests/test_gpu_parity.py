@@ -71,9 +71,11 @@ def test_linear_flow_flowmap_and_ftle(F, prec, dim):
     P = np.eye(dim) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
     P = np.linalg.matrix_power(P, 150)
     x0 = m.coords.astype(np.float64)
-    ph = phi.double().cpu().numpy()
     if prec == "fp32c":
+        ph = F.flowmap_pairs(phi, dim, m.n_nodes).double().cpu().numpy()
         ph = ph[..., 0] + ph[..., 1]
+    else:
+        ph = phi.double().cpu().numpy()
     assert np.abs(ph - P @ x0).max() < (1e-12 if prec == "fp64" else 1e-6)
     smax = np.linalg.svd(P, compute_uv=False)[0]
     expect = math.log(smax) / T
@@ -123,7 +125,7 @@ def test_flowmap_parity_fp32c(F):
     dm = F.DeviceMesh.from_mesh(w.mesh)
     phi = F.flowmap_empty(2, w.mesh.n_nodes, "fp32c")
     F.ftle_advect(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi)
-    ph = phi.double().cpu().numpy()
+    ph = F.flowmap_pairs(phi, 2, w.mesh.n_nodes).double().cpu().numpy()
     ph = ph[..., 0] + ph[..., 1]
     ref = O.advect(w.flow.kind, w.flow.params, w.mesh.coords, w.T, w.dt)
     err = np.abs(ph - ref)
@@ -264,7 +266,7 @@ def test_float_float_readvection_matches_fp64_flowmap(F):
     ws = out["workspace"].cpu().numpy()
     marked = np.frombuffer(ws[off: off + 4 * cnt["n_readvected"]].tobytes(), dtype=np.int32)
     assert len(np.unique(marked)) == len(marked) and marked.min() >= 0 and marked.max() < n
-    ph = out["phi"].double().cpu().numpy()
+    ph = F.flowmap_pairs(out["phi"], 2, n).double().cpu().numpy()
     ph = ph[..., 0] + ph[..., 1]
     ref = O.advect(w.flow.kind, w.flow.params, w.mesh.coords[:, marked], w.T, w.dt)
     err = np.abs(ph[:, marked] - ref).max()
@@ -298,3 +300,28 @@ def test_fixed_width_list_rejects_long_rows(F):
     with pytest.raises(F.FTLEError) as e:
         dm.attach_ell(8)  # Kuhn rows have 14 neighbours
     assert e.value.status == F.FTLE_ERANGE
+
+
+@pytest.mark.parametrize("preset,scale", [(1, 1 / 16), (2, 1 / 16)])
+def test_gradient_records_match_flowmap_pairs(F, preset, scale):
+    """The 32-byte gradient records after the (hi, lo) pairs hold the node's float coordinates,
+    the hi parts exactly and the lo parts (two of them in bfloat16 in 3D) as documented."""
+    w = I.preset(preset, scale=scale)
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    n, dim = w.mesh.n_nodes, w.mesh.dim
+    phi = F.flowmap_empty(dim, n, "fp32c")
+    F.ftle_advect(dm, w.flow, 0.0, 1.0, w.dt, "fp32c", phi)
+    pairs = F.flowmap_pairs(phi, dim, n).cpu().numpy()
+    off = (8 * dim * n + 255) // 256 * 256 // 4
+    rec = phi[off: off + 8 * n].cpu().numpy().reshape(n, 8)
+    assert np.array_equal(rec[:, :dim], w.mesh.coords.T)
+    if dim == 2:
+        assert np.array_equal(rec[:, 2:4], pairs[:, :, 0].T) and np.array_equal(rec[:, 4:6], pairs[:, :, 1].T)
+    else:
+        assert np.array_equal(rec[:, 3], pairs[0, :, 0]) and np.array_equal(rec[:, 4:6], pairs[1:, :, 0].T)
+        assert np.array_equal(rec[:, 6], pairs[0, :, 1])
+        words = rec[:, 7].view(np.uint32)
+        ly = (words << 16).view(np.float32)
+        lz = (words & 0xFFFF0000).view(np.float32)
+        for got, ref in ((ly, pairs[1, :, 1]), (lz, pairs[2, :, 1])):
+            assert np.all(np.abs(got - ref) <= np.abs(ref) * 2.0 ** -8 + 1e-45)
