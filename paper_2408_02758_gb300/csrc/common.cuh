@@ -90,15 +90,15 @@ constexpr float kPio2B = 0x1.fb4p-12f;
 constexpr float kPio2C = (float)(1.57079632679489661923 - (double)0x1.92p+0 - (double)0x1.fb4p-12);
 
 // sin(x), cos(x) at the compensated point xh + xl: x = k pi/2 + r, r carried as rh + rl (the
-// reduction residual and xl go to rl), minimax polynomials on rh, and the first-order
-// correction rl * (cos, -sin).  Valid for |x| < 2^11 * pi/2.
+// third part of pi/2 and xl go to rl), minimax polynomials on rh, and the first-order
+// correction rl * (cos, -sin).  Valid for |x| < 2^11 * pi/2.  Both reduction steps are exact:
+// for k != 0 (|x| > pi/4) xh, k A and k B are multiples of 2^-24 and |xh - k A|, |xh - k A - k B|
+// stay below 2, so each difference fits in a float; for k = 0 they return xh.
 __device__ __forceinline__ void fsincos_c(float xh, float xl, float& s, float& c) {
   const float t = fmaf(xh, 0.636619772367581343f, kRoundMagic);
   const float k = __fsub_rn(t, kRoundMagic);
-  const float r1 = fmaf(-k, kPio2A, xh);  // exact (Sterbenz; k * A exact)
-  float rh, re;
-  two_sum(r1, -k * kPio2B, rh, re);  // -k * B exact
-  const float rl = fmaf(-k, kPio2C, re) + xl;
+  const float rh = fmaf(-k, kPio2B, fmaf(-k, kPio2A, xh));
+  const float rl = fmaf(-k, kPio2C, xl);
   const float z = rh * rh;
   const float ps = fmaf(fmaf(fmaf(kRAD_S[3], z, kRAD_S[2]), z, kRAD_S[1]), z, kRAD_S[0]) * rh;
   const float pc = fmaf(fmaf(fmaf(fmaf(kRAD_C[4], z, kRAD_C[3]), z, kRAD_C[2]), z, kRAD_C[1]), z, kRAD_C[0]);
