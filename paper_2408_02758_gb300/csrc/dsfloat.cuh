@@ -6,6 +6,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "poly_coef.cuh"
 
 namespace ftle {
 
@@ -87,30 +88,6 @@ __device__ __forceinline__ dsf tc() {
   return ds_make(TaylorCoef<K, PI>::h, TaylorCoef<K, PI>::l);
 }
 
-// sin(s r) and cos(s r) for a small float-float r (|s r| <= pi/4), s = pi (PI) or 1.
-// Terms whose size stays below 2^-26 of the result are summed in float, the rest in
-// float-float (Horner in z = r^2).
-template <bool PI>
-__device__ __forceinline__ void ds_sincos_small(dsf r, dsf& s, dsf& c) {
-  const dsf z = ds_mul(r, r);
-  // sin: r * (c1 + z (c3 + z (c5 + z (c7 + z (c9 + z q))))), q = c11 + z (c13 + z c15) in float
-  float q = fmaf(fmaf(TaylorCoef<15, PI>::h, z.h, TaylorCoef<13, PI>::h), z.h, TaylorCoef<11, PI>::h);
-  dsf a = ds_add(tc<9, PI>(), ds_mul_f(z, q));
-  a = ds_add(tc<7, PI>(), ds_mul(z, a));
-  a = ds_add(tc<5, PI>(), ds_mul(z, a));
-  a = ds_add(tc<3, PI>(), ds_mul(z, a));
-  a = ds_add(tc<1, PI>(), ds_mul(z, a));
-  s = ds_mul(r, a);
-  // cos: 1 + z (c2 + z (c4 + z (c6 + z (c8 + z p)))), p = c10 + z (c12 + z (c14 + z c16)) in float
-  float p = fmaf(fmaf(fmaf(TaylorCoef<16, PI>::h, z.h, TaylorCoef<14, PI>::h), z.h, TaylorCoef<12, PI>::h), z.h,
-                 TaylorCoef<10, PI>::h);
-  dsf b = ds_add(tc<8, PI>(), ds_mul_f(z, p));
-  b = ds_add(tc<6, PI>(), ds_mul(z, b));
-  b = ds_add(tc<4, PI>(), ds_mul(z, b));
-  b = ds_add(tc<2, PI>(), ds_mul(z, b));
-  c = ds_add_f(ds_mul(z, b), 1.0f);
-}
-
 // Quarter-turn fix-up: (sin, cos) of (q * quarter + r) from (sin r, cos r), q taken mod 4.
 __device__ __forceinline__ void ds_quadrant(int q, dsf sr, dsf cr, dsf& s, dsf& c) {
   const int m = q & 3;
@@ -120,23 +97,51 @@ __device__ __forceinline__ void ds_quadrant(int q, dsf sr, dsf cr, dsf& s, dsf& 
   else { s = ds_neg(cr); c = sr; }
 }
 
-// sin(pi x), cos(pi x) of a float-float x: x = k/2 + r exactly, |r| <= 1/4.
+// sin and cos of a tiny float-float x (|x| <= 0.025): the terms that matter at float-float
+// precision (x, x^3/6, x^2/2) in float-float, the small remainder of each series in float.
+__device__ __forceinline__ void ds_sincos_tiny(dsf x, dsf& s, dsf& c) {
+  const dsf x2 = ds_mul(x, x);
+  // sin x = x + x^3 (-1/6 + x^2/120 - x^4/5040)
+  const float q = x2.h * fmaf(-x2.h, 1.0f / 5040.0f, 1.0f / 120.0f);
+  const dsf cs = ds_add_f(tc<3, false>(), q);
+  s = ds_add(x, ds_mul(ds_mul(x2, x), cs));
+  // cos x = 1 + x^2 (-1/2 + x^2/24 - x^4/720)
+  const float p = x2.h * fmaf(-x2.h, 1.0f / 720.0f, 1.0f / 24.0f);
+  c = ds_add_f(ds_mul(x2, ds_add_f(ds_make(-0.5f, 0.f), p)), 1.0f);
+}
+
+// (sin, cos)(a + u) from the tabulated (sin, cos)(a) and the tiny-argument pair of u.
+__device__ __forceinline__ void ds_rotate(const float4 t, dsf su, dsf cu, dsf& s, dsf& c) {
+  const dsf sa = ds_make(t.x, t.y), ca = ds_make(t.z, t.w);
+  s = ds_add(ds_mul(sa, cu), ds_mul(ca, su));
+  c = ds_add(ds_mul(ca, cu), ds_neg(ds_mul(sa, su)));
+}
+
+// sin(pi x), cos(pi x) of a float-float x: x = k/2 + r (|r| <= 1/4), r = j/64 + u (|u| <= 1/128),
+// both subtractions exact; (sin, cos)(pi j/64) from the table, pi u by the tiny series.
 __device__ __forceinline__ void ds_sincospi(dsf x, dsf& s, dsf& c) {
   const float k = rintf(2.0f * x.h);
-  const dsf r = ds_fast(x.h - 0.5f * k, x.l);  // x.h - k/2 is exact
-  dsf sr, cr;
-  ds_sincos_small<true>(r, sr, cr);
+  const dsf r = ds_fast(x.h - 0.5f * k, x.l);
+  const float j = rintf(64.0f * r.h);
+  const dsf u = ds_fast(r.h - j * (1.0f / 64.0f), r.l);
+  dsf su, cu, sr, cr;
+  ds_sincos_tiny(ds_mul(u, tc<1, true>()), su, cu);
+  ds_rotate(__ldg(reinterpret_cast<const float4*>(kDS_SINPI_TAB) + (int)j + 16), su, cu, sr, cr);
   ds_quadrant((int)k, sr, cr, s, c);
 }
 
-// sin(x), cos(x) of a float-float x: x = k pi/2 + r, the product k pi/2 in float-float.
+// sin(x), cos(x) of a float-float x: x = k pi/2 + r (the product in float-float), r = j/32 + u
+// (|u| <= 1/64, exact), (sin, cos)(j/32) from the table, u by the tiny series.
 __device__ __forceinline__ void ds_sincos(dsf x, dsf& s, dsf& c) {
   constexpr double kHalfPi = 1.57079632679489661923;
   const float k = rintf(x.h * (float)(2.0 / kPiD));
   const dsf pio2 = ds_make((float)kHalfPi, (float)(kHalfPi - (double)(float)kHalfPi));
   const dsf r = ds_add(x, ds_mul_f(pio2, -k));
-  dsf sr, cr;
-  ds_sincos_small<false>(r, sr, cr);
+  const float j = rintf(32.0f * r.h);
+  const dsf u = ds_fast(r.h - j * (1.0f / 32.0f), r.l);
+  dsf su, cu, sr, cr;
+  ds_sincos_tiny(u, su, cu);
+  ds_rotate(__ldg(reinterpret_cast<const float4*>(kDS_SIN_TAB) + (int)j + 26), su, cu, sr, cr);
   ds_quadrant((int)k, sr, cr, s, c);
 }
 

@@ -9,6 +9,10 @@ minimising the absolute error of the value (what enters the velocity) with float
 coefficients; the exchange runs in float64 on a dense grid, and the final coefficients are
 rounded to float32 and the achieved error is reported with float32 evaluation emulated.
 
+It also writes the float-float tables of the re-advection kernel: (sin, cos)(pi j/64) for
+j = -16..16 and (sin, cos)(j/32) for j = -26..26, each value split into a float pair h + l
+(h = fl(v), l = fl(v - h)) from the double-precision value.
+
 Run from the repository root:  python paper_2408_02758_gb300/csrc/gen_poly.py
 """
 from __future__ import annotations
@@ -105,6 +109,26 @@ def main():
         out.append(f"// {name}: sin = r * (s0 + z (s1 + ...)), cos = c0 + z (c1 + ...), z = r^2")
         out.append(f"constexpr float k{name}_S[{ns}] = {{" + ", ".join(f"{v:.9e}f" for v in s32) + "};")
         out.append(f"constexpr float k{name}_C[{nc}] = {{" + ", ".join(f"{v:.9e}f" for v in c32) + "};")
+    def pair(v):
+        h = np.float32(v)
+        return float(h), float(np.float32(v - float(h)))
+
+    rows = []
+    for j in range(-16, 17):
+        a = math.pi * j / 64
+        sh, sl = pair(math.sin(a))
+        ch, cl = pair(math.cos(a))
+        rows.append(f"  {{{sh:.9e}f, {sl:.9e}f, {ch:.9e}f, {cl:.9e}f}}")
+    out.append("// float-float (sin, cos)(pi j / 64), j = -16..16: {sin_h, sin_l, cos_h, cos_l}")
+    out.append("__device__ __align__(16) const float kDS_SINPI_TAB[33][4] = {\n" + ",\n".join(rows) + "};")
+    rows = []
+    for j in range(-26, 27):
+        a = j / 32
+        sh, sl = pair(math.sin(a))
+        ch, cl = pair(math.cos(a))
+        rows.append(f"  {{{sh:.9e}f, {sl:.9e}f, {ch:.9e}f, {cl:.9e}f}}")
+    out.append("// float-float (sin, cos)(j / 32), j = -26..26: {sin_h, sin_l, cos_h, cos_l}")
+    out.append("__device__ __align__(16) const float kDS_SIN_TAB[53][4] = {\n" + ",\n".join(rows) + "};")
     text = ("// Generated by gen_poly.py (Remez exchange, float32 coefficients); do not edit by hand.\n"
             "// " + "\n// ".join(report) + "\n#pragma once\n\nnamespace ftle {\n" + "\n".join(out) + "\n}  // namespace ftle\n")
     (HERE / "poly_coef.cuh").write_text(text)
