@@ -205,6 +205,24 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
  * longer than `width` (FTLE_ERANGE otherwise; nothing launched), then fills ell_idx on `stream`. */
 int ftle_ell_from_csr(const ftle_mesh* mesh, int32_t width, int32_t* ell_idx, void* stream);
 
+/* CSR neighbour lists built on the device from element connectivity (NEXT to the paper's host
+ * precomputation, Section 2.2, which names accelerating it as future work): nodes a != b are
+ * neighbours when some element lists both.  Rows come out sorted, symmetric and without the
+ * node itself, as the FTLE kernels expect.
+ *   elems      device int32 [n_elem][verts_per_elem] (2 = edges, 3 = triangles, 4 = tetrahedra)
+ *   max_row    bound on the raw entries of one node: (verts_per_elem - 1) x the number of elements
+ *              touching it (e.g. 3 x 24 for a Kuhn tetrahedral lattice)
+ *   row_ptr    device out [n_nodes + 1]; col_idx device out with room for nnz_cap entries
+ *   nnz_out    host out: the number of neighbour entries written
+ *   workspace  ftle_csr_workspace_bytes(n_nodes, max_row) bytes, 256-byte aligned
+ * Synchronous (returns after the lists are complete).  Errors: FTLE_EINVAL when an element names
+ * a vertex outside [0, n_nodes) (counted on the device, the element skipped); FTLE_ERANGE when a
+ * node exceeds max_row raw entries or nnz exceeds nnz_cap. */
+size_t ftle_csr_workspace_bytes(int64_t n_nodes, int32_t max_row);
+int ftle_csr_from_elements(int64_t n_nodes, int64_t n_elem, int32_t verts_per_elem, const int32_t* elems,
+                           int32_t max_row, int32_t* row_ptr, int32_t* col_idx, int64_t nnz_cap,
+                           int64_t* nnz_out, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Synchronous read of the counters at the start of `workspace` (waits for `stream`). */
 int ftle_read_counters(const void* workspace, ftle_counters* out, void* stream);
 

@@ -75,6 +75,9 @@ _SIGS = [
                                   POINTER(ftle_options), c_void_p]),
     ("ftle_read_counters", c_int, [c_void_p, POINTER(ftle_counters), c_void_p]),
     ("ftle_ell_from_csr", c_int, [POINTER(ftle_mesh), c_int32, c_void_p, c_void_p]),
+    ("ftle_csr_workspace_bytes", c_size_t, [c_int64, c_int32]),
+    ("ftle_csr_from_elements", c_int, [c_int64, c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int64,
+                                       POINTER(c_int64), c_void_p, c_size_t, c_void_p]),
     ("ftle_gradient_eig_noalloc", c_int, [POINTER(ftle_mesh), c_void_p, c_int32, c_double, c_void_p, c_void_p,
                                           POINTER(ftle_options), c_void_p]),
     ("ftle_batch_workspace_bytes", c_size_t, [c_int32, POINTER(ftle_mesh), c_int32]),
@@ -392,6 +395,20 @@ def ftle_batch(meshes, flows, T, dt: float, precision, outs, workspace, options:
                                           ctypes.byref(options) if options else None, _stream(stream)))
 
 
+def compute_pair(mesh: DeviceMesh, flow, T: float, dt: float, precision="fp32c", options: ftle_options | None = None,
+                 stream=None):
+    """Forward (horizon +|T|) and backward (-|T|) FTLE of one mesh from t = 0, as two instances of
+    one batched launch sequence: ridges of the forward field mark repelling structures, ridges of
+    the backward field attracting ones.  Returns (ftle_forward, ftle_backward), device float32."""
+    import torch
+
+    dev = mesh.coords.device
+    outs = [torch.empty(mesh.n_nodes, dtype=torch.float32, device=dev) for _ in range(2)]
+    ws = workspace_empty(ftle_batch_workspace_bytes([mesh, mesh], precision), device=dev)
+    ftle_batch([mesh, mesh], [flow, flow], [abs(T), -abs(T)], dt, precision, outs, ws, options=options, stream=stream)
+    return outs[0], outs[1]
+
+
 class BatchPlan:
     """A batch captured once into a CUDA graph (ftle_batch_plan_create) and replayed with launch()."""
 
@@ -449,3 +466,24 @@ def checkpoints_empty(dim: int, n_nodes: int, n_steps: int, ckpt_every: int, pre
     nbytes = ftle_checkpoint_bytes(dim, n_nodes, precision)
     dtype = torch.float64 if _prec(precision) == PREC["fp64"] else torch.float32
     return torch.empty((slots, nbytes // dtype.itemsize), dtype=dtype, device=device)
+
+
+# ------------------------------------------------------------------------------ mesh preparation
+
+
+def ftle_csr_from_elements(n_nodes: int, elems, max_row: int, nnz_cap: int | None = None, stream=None):
+    """CSR neighbour lists (row_ptr, col_idx device int32 tensors) of the node adjacency of a
+    device int32 element array [n_elem, verts_per_elem], built on the GPU."""
+    import torch
+
+    elems = elems.contiguous()
+    n_elem, v = int(elems.shape[0]), int(elems.shape[1])
+    cap = nnz_cap if nnz_cap is not None else n_elem * v * (v - 1)
+    row_ptr = torch.empty(n_nodes + 1, dtype=torch.int32, device=elems.device)
+    col_idx = torch.empty(max(cap, 1), dtype=torch.int32, device=elems.device)
+    ws = workspace_empty(int(lib().ftle_csr_workspace_bytes(n_nodes, max_row)), device=elems.device)
+    nnz = c_int64(0)
+    _check("ftle_csr_from_elements",
+           lib().ftle_csr_from_elements(n_nodes, n_elem, v, _ptr(elems), max_row, _ptr(row_ptr), _ptr(col_idx), cap,
+                                        ctypes.byref(nnz), _ptr(ws), ws.numel(), _stream(stream)))
+    return row_ptr, col_idx[: nnz.value]

@@ -115,6 +115,29 @@ def lattice_csr(shape, stencil: int):
     return row_ptr, col_idx
 
 
+def lattice_elements(shape, stencil: int) -> np.ndarray:
+    """Element connectivity (int32 [n_elem, verts]) of the lattice meshes whose mesh edges the TRI
+    and KUHN stencils list: two triangles per cell split along the (i,j)-(i+1,j+1) diagonal, or the
+    six Kuhn tetrahedra 0 -> e_a -> e_a + e_b -> (1,1,1) of each hex."""
+    if stencil == TRI:
+        nx, ny = shape
+        i, j = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1), indexing="xy")
+        v00 = (i + nx * j).ravel()
+        v10, v11, v01 = v00 + 1, v00 + 1 + nx, v00 + nx
+        tri = np.concatenate([np.stack([v00, v10, v11], 1), np.stack([v00, v11, v01], 1)])
+        return np.ascontiguousarray(tri, dtype=np.int32)
+    if stencil == KUHN:
+        nx, ny, nz = shape
+        i, j, k = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1), np.arange(nz - 1), indexing="ij")
+        c = (i + nx * (j + ny * k)).ravel()
+        e = [1, nx, nx * ny]
+        out = []
+        for a, b, cc in [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]:
+            out.append(np.stack([c, c + e[a], c + e[a] + e[b], c + e[a] + e[b] + e[cc]], 1))
+        return np.ascontiguousarray(np.concatenate(out), dtype=np.int32)
+    raise ValueError("element lists exist for the TRI and KUHN stencils")
+
+
 def make_mesh(shape, lo, hi, stencil: int, jitter: float = 0.0, seed: int = BASE_SEED,
               coord_dtype=np.float32) -> Mesh:
     """Lattice mesh with jittered nodes; coordinates rounded once to ``coord_dtype``.

@@ -114,3 +114,25 @@ def test_autotuned_options_give_identical_results(batch):
     torch.cuda.synchronize()
     for o, r in zip(outs, ref):
         assert torch.equal(o, r)
+
+
+@pytest.mark.parametrize("preset,T", [(1, 5.0), (2, 2.0)])
+def test_forward_backward_pair_in_one_batch(preset, T):
+    """compute_pair runs +T and -T as one batch: each field equals its single run and the FP64
+    oracle at the same horizon."""
+    import torch
+
+    from paper_2408_02758_gb300 import ftle
+
+    w = I.preset(preset, scale=1 / 32 if preset == 1 else 1 / 16)
+    dm = ftle.DeviceMesh.from_mesh(w.mesh)
+    fwd, bwd = ftle.compute_pair(dm, w.flow, T, w.dt, "fp32c")
+    torch.cuda.synchronize()
+    x0 = w.mesh.coords.astype(np.float64)
+    for got, horizon in ((fwd, T), (bwd, -T)):
+        got = got.double().cpu().numpy()
+        single = ftle.compute(dm, w.flow, horizon, w.dt, "fp32c").double().cpu().numpy()
+        assert np.all((got == single) | (np.abs(got - single) <= 1e-9 * np.abs(single)) | (np.isnan(got) & np.isnan(single)))
+        o = O.ftle(w.flow.kind, w.flow.params, x0, w.mesh.row_ptr, w.mesh.col_idx, horizon, w.dt)
+        rep = compare(got, o["ftle"], o["lam"])
+        assert rep["ok"], rep

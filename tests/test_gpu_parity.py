@@ -325,3 +325,28 @@ def test_gradient_records_match_flowmap_pairs(F, preset, scale):
         lz = (words & 0xFFFF0000).view(np.float32)
         for got, ref in ((ly, pairs[1, :, 1]), (lz, pairs[2, :, 1])):
             assert np.all(np.abs(got - ref) <= np.abs(ref) * 2.0 ** -8 + 1e-45)
+
+
+@pytest.mark.parametrize("shape,stencil,max_row", [((37, 23), I.TRI, 16), ((9, 8, 7), I.KUHN, 80), ((64, 64, 64), I.KUHN, 80)])
+def test_gpu_csr_from_elements_matches_host_lists(F, shape, stencil, max_row):
+    """Neighbour lists built on the GPU from triangles / tetrahedra equal the host lists exactly."""
+    import torch
+
+    m = I.make_mesh(shape, (0,) * len(shape), (1,) * len(shape), stencil, 0.2, 3)
+    el = torch.from_numpy(I.lattice_elements(shape, stencil)).cuda()
+    rp, ci = F.ftle_csr_from_elements(m.n_nodes, el, max_row)
+    assert np.array_equal(rp.cpu().numpy(), m.row_ptr)
+    assert np.array_equal(ci.cpu().numpy(), m.col_idx)
+
+
+def test_gpu_csr_from_elements_rejects_bad_input(F):
+    import torch
+
+    el = torch.tensor([[0, 1, 2], [1, 2, 7]], dtype=torch.int32, device="cuda")  # vertex 7 >= n_nodes
+    with pytest.raises(F.FTLEError) as e:
+        F.ftle_csr_from_elements(4, el, 8)
+    assert e.value.status == F.FTLE_EINVAL
+    el = torch.tensor([[0, 1, 2], [0, 2, 3], [0, 3, 1]], dtype=torch.int32, device="cuda")
+    with pytest.raises(F.FTLEError) as e:
+        F.ftle_csr_from_elements(4, el, 3)  # node 0 has 6 raw entries
+    assert e.value.status == F.FTLE_ERANGE

@@ -104,3 +104,19 @@ def test_presets_shapes():
         assert b.T in (5.0, 10.0, 15.0, 20.0)
         A, eps, om = b.flow.params[:3]
         assert A == 0.1 and 0 <= eps <= 0.5 and math.pi / 10 <= om <= math.pi / 2
+
+
+@pytest.mark.parametrize("shape,stencil", [((7, 5), I.TRI), ((4, 5, 3), I.KUHN)])
+def test_element_lists_span_the_stencil_edges(shape, stencil):
+    """The element lists' edges are exactly the stencil's neighbour pairs (host check of the
+    connectivity the GPU adjacency builder consumes)."""
+    m = I.make_mesh(shape, (0,) * len(shape), (1,) * len(shape), stencil, 0.0, 1)
+    el = I.lattice_elements(shape, stencil)
+    pairs = set()
+    for row in el:
+        for a in row:
+            for b in row:
+                if a != b:
+                    pairs.add((int(a), int(b)))
+    rows = np.repeat(np.arange(m.n_nodes), np.diff(m.row_ptr))
+    assert pairs == set(zip(rows.tolist(), m.col_idx.tolist()))
