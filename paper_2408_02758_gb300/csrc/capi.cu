@@ -181,6 +181,13 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
   a.h2_32 = (float)(0.5 * a.h);
   a.h6_32 = (float)(a.h / 6.0);
   memcpy(a.p, f->p, sizeof a.p);
+  for (int d = 0; d < 3; ++d) {
+    double scale = 1.0;  // the compensated double gyre carries u / (-pi A) and v / (pi A)
+    if (f->kind == FTLE_FLOW_DOUBLE_GYRE && d < 2) scale = (d == 0 ? -kPi : kPi) * f->p[0];
+    a.hs[d][0] = (float)(0.5 * a.h * scale);
+    a.hs[d][1] = (float)(a.h * scale);
+    a.hs[d][2] = (float)(a.h / 6.0 * scale);
+  }
   return a;
 }
 

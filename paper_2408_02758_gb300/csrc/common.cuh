@@ -192,8 +192,8 @@ __device__ __forceinline__ void dg_vel32(float piA, float a, float b, float x, f
 // --- double gyre at the compensated point (xh + xl, yh + yl).  f = x (a x + b) is formed with
 // error-free products and sums, so its rounding does not act as a position error; sin/cos of
 // pi (fh + fl) take the first-order correction pi fl cos / -pi fl sin.  b = bh + bl.
-__device__ __forceinline__ void dg_vel32c(float piA, float a, float bh, float bl, float xh, float xl,
-                                          float yh, float yl, float& u, float& v) {
+__device__ __forceinline__ void dg_base32c(float a, float bh, float bl, float xh, float xl, float yh, float yl,
+                                           float& sf2, float& cf2, float& sy2, float& cy2, float& fx) {
   const float kPiF = 3.14159265358979323846f;
   float p = a * xh;
   float pe = fmaf(a, xh, -p);  // a xh = p + pe exactly
@@ -203,15 +203,37 @@ __device__ __forceinline__ void dg_vel32c(float piA, float a, float bh, float bl
   float fh = g * xh;
   float fe = fmaf(g, xh, -fh);               // g xh = fh + fe exactly
   float fl = fe + fmaf(ge, xh, g * xl);      // f = fh + fl
-  float fx = fmaf(2.0f * a, xh, bh + fmaf(2.0f * a, xl, bl));
+  fx = fmaf(2.0f * a, xh, bh + fmaf(2.0f * a, xl, bl));
   float sf, cf, sy, cy;
   fsincospi(fh, sf, cf);
   fsincospi(yh, sy, cy);
   float df = kPiF * fl, dy = kPiF * yl;
-  float sf2 = fmaf(df, cf, sf), cf2 = fmaf(-df, sf, cf);
-  float sy2 = fmaf(dy, cy, sy), cy2 = fmaf(-dy, sy, cy);
-  u = -piA * sf2 * cy2;
-  v = piA * cf2 * sy2 * fx;
+  sf2 = fmaf(df, cf, sf);
+  cf2 = fmaf(-df, sf, cf);
+  sy2 = fmaf(dy, cy, sy);
+  cy2 = fmaf(-dy, sy, cy);
+}
+
+__device__ __forceinline__ void dg_vel32c(float piA, float a, float bh, float bl, float xh, float xl,
+                                          float yh, float yl, float& u, float& v) {
+  float sf, cf, sy, cy, fx;
+  dg_base32c(a, bh, bl, xh, xl, yh, yl, sf, cf, sy, cy, fx);
+  u = -piA * sf * cy;
+  v = piA * cf * sy * fx;
+}
+
+// (sin, cos)(phi + th) from (s0, c0) = (sin, cos)(phi) by the angle-addition formulas, with the
+// small angle's sin th = th - th^3/6 and cos th - 1 = -th^2/2 + th^4/24 (Taylor).  For |th| <=
+// kRotMax the dropped terms are below th^5/120 <= 2.7e-9 and th^6/720 <= 2.2e-11; the small
+// corrections are formed first and added to s0, c0 with one rounding each.
+constexpr float kRotMax = 0.05f;
+
+__device__ __forceinline__ void rotate_small(float s0, float c0, float th, float& s, float& c) {
+  const float t2 = th * th;
+  const float st = fmaf(th * t2, -1.0f / 6.0f, th);
+  const float cm = t2 * fmaf(t2, 1.0f / 24.0f, -0.5f);
+  s = s0 + fmaf(s0, cm, c0 * st);
+  c = c0 + fmaf(c0, cm, -(s0 * st));
 }
 
 // --- double gyre, double precision

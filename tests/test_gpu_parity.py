@@ -133,6 +133,21 @@ def test_flowmap_parity_fp32c(F):
     assert np.median(err) < 1e-6 and err.max() < 5e-3
 
 
+@pytest.mark.parametrize("preset,scale,T,dt", [(1, 1 / 16, 5.0, 0.1), (2, 1 / 8, 2.0, 0.05)])
+def test_large_steps_mix_rotated_and_full_stages(F, preset, scale, T, dt):
+    """Steps long enough that the stage angles of fast nodes exceed the small-angle bound, so
+    lanes of one warp take the rotated and the fully evaluated stages side by side; both agree
+    with the FP64 oracle's RK4 at the same step."""
+    w = I.preset(preset, scale=scale)
+    ft, lam, phi, cnt = run_gpu(F, w.mesh, w.flow, T, dt, "fp32c")
+    o = _oracle_full(w.mesh, w.flow, T, dt)
+    rep = compare(ft, o["ftle"], o["lam"])
+    assert rep["ok"], (rep, cnt)
+    ph = F.flowmap_pairs(phi, w.mesh.dim, w.mesh.n_nodes).double().cpu().numpy()
+    err = np.abs(ph[..., 0] + ph[..., 1] - o["phi"])
+    assert err.max() < 1e-6, err.max()
+
+
 @pytest.mark.parametrize("idx,n_sample", [(1, 3000), (2, 600)])
 def test_full_size_workload_sampled(F, idx, n_sample):
     """The benchmark's workloads at full size (2.1M-node triangle mesh; 16.7M-node tet mesh), in the
