@@ -26,6 +26,8 @@ struct AdvArgs {
   float h32, h2_32, h6_32;     // h, h/2, h/6 rounded once
   float hs[3][3];              // per component: (h/2, h, h/6) times that component's velocity
                                // scale, rounded once (compensated double gyre: -pi A, pi A; else 1)
+  float hs_pi[2];              // double gyre: pi (h/2, h) pi A, the y angle per unit of carried v
+  float habc[3][3];            // ABC: (h/2, h, h/6) times (A, B, C), rounded once
   double p[12];                // flow parameters
   const int32_t* list;         // nullable: process list[0 .. *list_count)
   const unsigned long long* list_count;
@@ -178,21 +180,23 @@ __device__ __forceinline__ void comp_add(float xh, float d, float& s, float& e) 
 // term).  The stage's (sin, cos)(pi f) and (sin, cos)(pi y) are stage one's pairs rotated by pi
 // times the differences; a lane whose angle exceeds kRotMax evaluates the stage in full at the
 // compensated stage point instead.  Returns the velocity without its factors -pi A and pi A.
-__device__ __forceinline__ void dg_stage_rot(const Coef& cs, float e1, float dg, float dx, float dy, float sf,
-                                             float cf, float sy, float cy, const float* xh, const float* xl,
-                                             float& ku, float& kv) {
+// The y increment arrives as kv with two scales: hy (dy = hy kv) and hy_pi (the angle pi dy).
+__device__ __forceinline__ void dg_stage_rot(const Coef& cs, float e1, float dg, float dx, float kv_prev, float hy,
+                                             float hy_pi, float sf, float cf, float sy, float cy, const float* xh,
+                                             const float* xl, float& ku, float& kv) {
   const float kPiF = 3.14159265358979323846f;
-  const float tf = kPiF * fmaf(dx, fmaf(cs.a, e1 + dx, 1.0f), dg);
-  const float ty = kPiF * dy;
+  const float w = fmaf(cs.a, e1 + dx, 1.0f);  // 1 + a_s (2 (x0 - 1) + dx)
+  const float tf = kPiF * fmaf(dx, w, dg);
+  const float ty = hy_pi * kv_prev;
   float sfs, cfs, sys, cys, fxs;
   if (fmaxf(fabsf(tf), fabsf(ty)) <= kRotMax) {
     rotate_small(sf, cf, tf, sfs, cfs);
     rotate_small(sy, cy, ty, sys, cys);
-    fxs = fmaf(cs.a, fmaf(2.0f, dx, e1), 1.0f);  // f_s'(x0 + dx) = 1 + 2 a_s (x0 + dx - 1)
+    fxs = fmaf(cs.a, dx, w);  // f_s'(x0 + dx) = 1 + 2 a_s (x0 + dx - 1)
   } else {
     float ph, pe, qh, qe;
     two_sum(xh[0], dx, ph, pe);
-    two_sum(xh[1], dy, qh, qe);
+    two_sum(xh[1], hy * kv_prev, qh, qe);
     dg_base32c(cs.a, cs.bh, cs.bl, ph, pe + xl[0], qh, qe + xl[1], sfs, cfs, sys, cys, fxs);
   }
   ku = sfs * cys;
@@ -202,7 +206,7 @@ __device__ __forceinline__ void dg_stage_rot(const Coef& cs, float e1, float dg,
 // ABC stage two, three or four of the compensated step: stage one's (sin, cos) of x, y, z rotated
 // by the stage increments d (radians); full evaluation at the compensated stage point when an
 // increment exceeds kRotMax.
-__device__ __forceinline__ void abc_stage_rot(const AdvArgs& a, const float* d, const float* s0, const float* c0,
+__device__ __forceinline__ void abc_stage_rot(const float* co, const float* d, const float* s0, const float* c0,
                                               const float* xh, const float* xl, float* k) {
   float s[3], c[3];
   if (fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))) <= kRotMax) {
@@ -216,10 +220,10 @@ __device__ __forceinline__ void abc_stage_rot(const AdvArgs& a, const float* d, 
       fsincos_c(ph, pe + xl[q], s[q], c[q]);
     }
   }
-  const float A = (float)a.p[0], B = (float)a.p[1], C = (float)a.p[2];
-  k[0] = fmaf(A, s[2], C * c[1]);
-  k[1] = fmaf(B, s[0], A * c[2]);
-  k[2] = fmaf(C, s[1], B * c[0]);
+  // co = (A, B, C) times the scale of the value returned (the next stage's increment, or h/6)
+  k[0] = fmaf(co[0], s[2], co[2] * c[1]);
+  k[1] = fmaf(co[1], s[0], co[0] * c[2]);
+  k[2] = fmaf(co[2], s[1], co[1] * c[0]);
 }
 
 // Advance one node by one classic RK4 step (stages at t, t + h/2, t + h/2, t + h, with the
@@ -257,16 +261,17 @@ __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const
 #pragma unroll
     for (int d = 0; d < DIM; ++d) xh[d] = fmaf(a.h6_32, fmaf(2.f, k2v[d] + k3v[d], k1v[d] + k4v[d]), xh[d]);
   } else if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE) {  // P32C, stages two to four by rotation
-    float sf, cf, sy, cy, fx;
-    dg_base32c(c0.a, c0.bh, c0.bl, xh[0], xl[0], xh[1], xl[1], sf, cf, sy, cy, fx);
+    float sf, cf, sy, cy, fx_unused;
+    dg_base32c(c0.a, c0.bh, c0.bl, xh[0], xl[0], xh[1], xl[1], sf, cf, sy, cy, fx_unused);
+    const float e1 = fmaf(2.0f, xh[0], -2.0f);        // 2 (x0 - 1)
+    const float fx = fmaf(c0.a, e1, 1.0f);            // f_0'(x0) = 1 + 2 a_0 (x0 - 1)
     const float k1u = sf * cy, k1v = cf * sy * fx;
-    const float e1 = fmaf(2.0f, xh[0], -2.0f);
     const float g0 = xh[0] * (xh[0] - 2.0f);
     const float dg1 = (c1.a - c0.a) * g0, dg2 = (c2.a - c0.a) * g0;
     float k2u, k2v, k3u, k3v, k4u, k4v;
-    dg_stage_rot(c1, e1, dg1, a.hs[0][0] * k1u, a.hs[1][0] * k1v, sf, cf, sy, cy, xh, xl, k2u, k2v);
-    dg_stage_rot(c1, e1, dg1, a.hs[0][0] * k2u, a.hs[1][0] * k2v, sf, cf, sy, cy, xh, xl, k3u, k3v);
-    dg_stage_rot(c2, e1, dg2, a.hs[0][1] * k3u, a.hs[1][1] * k3v, sf, cf, sy, cy, xh, xl, k4u, k4v);
+    dg_stage_rot(c1, e1, dg1, a.hs[0][0] * k1u, k1v, a.hs[1][0], a.hs_pi[0], sf, cf, sy, cy, xh, xl, k2u, k2v);
+    dg_stage_rot(c1, e1, dg1, a.hs[0][0] * k2u, k2v, a.hs[1][0], a.hs_pi[0], sf, cf, sy, cy, xh, xl, k3u, k3v);
+    dg_stage_rot(c2, e1, dg2, a.hs[0][1] * k3u, k3v, a.hs[1][1], a.hs_pi[1], sf, cf, sy, cy, xh, xl, k4u, k4v);
     const float inc[2] = {a.hs[0][2] * fmaf(2.f, k2u + k3u, k1u + k4u), a.hs[1][2] * fmaf(2.f, k2v + k3v, k1v + k4v)};
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
@@ -276,27 +281,20 @@ __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const
       xl[d] = e;
     }
   } else if constexpr (KIND == FTLE_FLOW_ABC) {  // P32C, stages two to four by rotation
-    float s0[3], c0v[3], k1v[3], k2v[3], k3v[3], k4v[3], d[3];
+    // stage increments d1 = h/2 k1, d2 = h/2 k2, d3 = h k3 and e4 = h/6 k4 straight from the
+    // folded constants; the step adds (d1 + 2 d2 + d3) / 3 + e4 = h/6 (k1 + 2 k2 + 2 k3 + k4)
+    float s0[3], c0v[3], d1[3], d2[3], d3[3], e4[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) fsincos_c(xh[q], xl[q], s0[q], c0v[q]);
-    {
-      const float A = (float)a.p[0], B = (float)a.p[1], C = (float)a.p[2];
-      k1v[0] = fmaf(A, s0[2], C * c0v[1]);
-      k1v[1] = fmaf(B, s0[0], A * c0v[2]);
-      k1v[2] = fmaf(C, s0[1], B * c0v[0]);
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) d[q] = a.hs[q][0] * k1v[q];
-    abc_stage_rot(a, d, s0, c0v, xh, xl, k2v);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) d[q] = a.hs[q][0] * k2v[q];
-    abc_stage_rot(a, d, s0, c0v, xh, xl, k3v);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) d[q] = a.hs[q][1] * k3v[q];
-    abc_stage_rot(a, d, s0, c0v, xh, xl, k4v);
+    d1[0] = fmaf(a.habc[0][0], s0[2], a.habc[0][2] * c0v[1]);
+    d1[1] = fmaf(a.habc[0][1], s0[0], a.habc[0][0] * c0v[2]);
+    d1[2] = fmaf(a.habc[0][2], s0[1], a.habc[0][1] * c0v[0]);
+    abc_stage_rot(a.habc[0], d1, s0, c0v, xh, xl, d2);
+    abc_stage_rot(a.habc[1], d2, s0, c0v, xh, xl, d3);
+    abc_stage_rot(a.habc[2], d3, s0, c0v, xh, xl, e4);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const float inc = a.hs[q][2] * fmaf(2.f, k2v[q] + k3v[q], k1v[q] + k4v[q]);
+      const float inc = fmaf(fmaf(2.f, d2[q], d1[q] + d3[q]), 1.0f / 3.0f, e4[q]);
       float s, e;
       comp_add<KIND>(xh[q], inc + xl[q], s, e);
       xh[q] = s;

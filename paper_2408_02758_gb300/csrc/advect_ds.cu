@@ -137,6 +137,89 @@ __global__ void __launch_bounds__(32) k_advect_ds(AdvArgs a) {
   }
 }
 
+// Double gyre in 2D with two lanes per node: lane p = 0 carries x and evaluates sin/cos(pi f),
+// lane p = 1 carries y and evaluates sin/cos(pi y).  Both lanes run one instruction stream: the
+// argument is f = (a_p x + b_p) x with (a_p, b_p) = (a, 1 - 2a) for p = 0 and (0, 1) for p = 1,
+// so lane 1's argument is y and its slope is 1.  Each lane then needs only the partner's cosine
+// and slope (four floats by shuffle):
+//   u = -pi A sin(pi f) cos(pi y),  v = pi A sin(pi y) cos(pi f) f_x,
+// and updates its own coordinate.  The node's two float-float chains run on two lanes instead of
+// interleaving in one, which halves the instructions a lane issues per stage; the arithmetic is
+// the single-lane kernel's up to the order of the velocity product.
+template <typename CT>
+__global__ void __launch_bounds__(32) k_advect_ds_dg_pair(AdvArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dsf* tab = reinterpret_cast<dsf*>(smem_raw);
+  const int64_t count = a.list ? (int64_t)*a.list_count : a.n;
+  const int nchunks = (a.nsteps + kAdvChunk - 1) / kAdvChunk;
+  const int p = threadIdx.x & 1;
+  const dsf piA = ds_from_double((p ? kPi : -kPi) * a.p[0]);
+  const dsf h = ds_from_double(a.h), h2 = ds_from_double(0.5 * a.h), h6 = ds_from_double(a.h / 6.0);
+  const dsf one = ds_make(1.0f, 0.0f);
+  const dsf third = ds_from_double(1.0 / 3.0);
+  bool table_valid = false;
+
+  const int lanes = (a.lanes > 0 && a.lanes < (int)blockDim.x) ? max(2, a.lanes & ~1) : (int)blockDim.x;
+  const int per_block = lanes / 2;
+  for (int64_t base = (int64_t)blockIdx.x * per_block; base < count; base += (int64_t)gridDim.x * per_block) {
+    const int64_t slot = base + (threadIdx.x >> 1);
+    // both lanes of a pair are active or idle together; idle pairs integrate a dummy node so
+    // that every lane reaches each shuffle
+    const bool active = (int)threadIdx.x < lanes && slot < count;
+    const int64_t i = active ? (a.list ? (int64_t)a.list[slot] : slot) : 0;
+    dsf x = ds_from_double(active ? (double)__ldg(reinterpret_cast<const CT*>(a.coords) + p * a.n_mesh + i) : 0.0);
+    const float x0 = x.h;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int k0 = ch * kAdvChunk;
+      const int k1 = min(a.nsteps, k0 + kAdvChunk);
+      if (!(table_valid && nchunks == 1)) {
+        __syncthreads();
+        for (int m = threadIdx.x; m <= 2 * (k1 - k0); m += blockDim.x)
+          tab[m] = ds_from_double(a.p[1] * sin(a.p[2] * (a.t0 + 0.5 * a.h * (double)(2 * k0 + m))));
+        __syncthreads();
+        table_valid = true;
+      }
+      // hc times this lane's velocity component at y: the scale (a stage's step fraction times
+      // -pi A or pi A times the partner's slope) is formed while the sine and cosine evaluate, so
+      // two products follow them on the dependency chain
+      auto vel = [&](const dsf& y, const dsf& ca, const dsf& hc) -> dsf {
+        const dsf ap = p ? ds_make(0.f, 0.f) : ca;
+        const dsf bp = p ? one : ds_add_f(ds_make(-2.0f * ca.h, -2.0f * ca.l), 1.0f);
+        const dsf t1 = ds_mul(ap, y);
+        const dsf f = ds_mul(ds_add(t1, bp), y);
+        const dsf fx = ds_add(ds_make(2.0f * t1.h, 2.0f * t1.l), bp);
+        const dsf fq = ds_make(__shfl_xor_sync(0xffffffffu, fx.h, 1), __shfl_xor_sync(0xffffffffu, fx.l, 1));
+        const dsf g = ds_make(p ? fq.h : 1.0f, p ? fq.l : 0.0f);
+        const dsf scale = ds_mul(ds_mul(piA, g), hc);
+        dsf sn, cs;
+        ds_sincospi(f, sn, cs);
+        const dsf cq = ds_make(__shfl_xor_sync(0xffffffffu, cs.h, 1), __shfl_xor_sync(0xffffffffu, cs.l, 1));
+        return ds_mul(ds_mul(sn, cq), scale);
+      };
+      for (int k = k0; k < k1; ++k) {
+        const int m = 2 * (k - k0);
+        const dsf c0 = tab[m], c1 = tab[m + 1], c2 = tab[m + 2];
+        // d1 = h/2 k1, d2 = h/2 k2, d3 = h k3, e4 = h/6 k4; the step adds (d1 + 2 d2 + d3) / 3 + e4
+        const dsf d1 = vel(x, c0, h2);
+        const dsf d2 = vel(ds_add(x, d1), c1, h2);
+        const dsf d3 = vel(ds_add(x, d2), c1, h);
+        const dsf e4 = vel(ds_add(x, d3), c2, h6);
+        const dsf sum = ds_add(ds_add(d1, d3), ds_make(2.0f * d2.h, 2.0f * d2.l));
+        x = ds_add(x, ds_add(ds_mul(sum, third), e4));
+      }
+    }
+    const float q0 = __shfl_xor_sync(0xffffffffu, x0, 1);
+    const float qh = __shfl_xor_sync(0xffffffffu, x.h, 1), ql = __shfl_xor_sync(0xffffffffu, x.l, 1);
+    if (active) {
+      reinterpret_cast<float2*>(a.out)[p * a.n_mesh + i] = make_float2(x.h, x.l);
+      if (a.rec && p == 0) {
+        const float xs[2] = {x0, q0}, ph[2] = {x.h, qh}, pl[2] = {x.l, ql};
+        store_record<2>(a.rec, i, xs, ph, pl);
+      }
+    }
+  }
+}
+
 // Batched re-advection: the list holds (instance, node) pairs, so lanes of one warp may belong
 // to different instances; each lane forms its own double-gyre coefficient a(t_m) =
 // eps sin(omega t_m) in float-float (t_m = t0 + m h/2) instead of reading a shared table.
@@ -229,8 +312,12 @@ static void ds_dispatch(bool coord64, const AdvArgs& args, int grid, int block, 
 int launch_advect_ds(int kind, int dim, bool coord64, const AdvArgs& args, int grid, int block,
                      cudaStream_t stream) {
   const size_t smem = advect_smem_bytes(kind, P32, args.nsteps);  // one float pair per half step
-  if (kind == FTLE_FLOW_DOUBLE_GYRE && dim == 2) ds_dispatch<FTLE_FLOW_DOUBLE_GYRE, 2>(coord64, args, grid, block, smem, stream);
-  else if (kind == FTLE_FLOW_ABC && dim == 3) ds_dispatch<FTLE_FLOW_ABC, 3>(coord64, args, grid, block, smem, stream);
+  if (kind == FTLE_FLOW_DOUBLE_GYRE && dim == 2) {
+    if (coord64)
+      k_advect_ds_dg_pair<double><<<2 * grid, block, smem, stream>>>(args);
+    else
+      k_advect_ds_dg_pair<float><<<2 * grid, block, smem, stream>>>(args);
+  } else if (kind == FTLE_FLOW_ABC && dim == 3) ds_dispatch<FTLE_FLOW_ABC, 3>(coord64, args, grid, block, smem, stream);
   else if (kind == FTLE_FLOW_LINEAR && dim == 2) ds_dispatch<FTLE_FLOW_LINEAR, 2>(coord64, args, grid, block, smem, stream);
   else if (kind == FTLE_FLOW_LINEAR && dim == 3) ds_dispatch<FTLE_FLOW_LINEAR, 3>(coord64, args, grid, block, smem, stream);
   else if (kind == FTLE_FLOW_SADDLE && dim == 2) ds_dispatch<FTLE_FLOW_SADDLE, 2>(coord64, args, grid, block, smem, stream);

@@ -188,6 +188,13 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
     a.hs[d][1] = (float)(a.h * scale);
     a.hs[d][2] = (float)(a.h / 6.0 * scale);
   }
+  if (f->kind == FTLE_FLOW_DOUBLE_GYRE) {
+    a.hs_pi[0] = (float)(kPi * 0.5 * a.h * kPi * f->p[0]);
+    a.hs_pi[1] = (float)(kPi * a.h * kPi * f->p[0]);
+  }
+  const double hsc[3] = {0.5 * a.h, a.h, a.h / 6.0};
+  for (int s = 0; s < 3; ++s)
+    for (int q = 0; q < 3; ++q) a.habc[s][q] = (float)(hsc[s] * f->p[q]);
   return a;
 }
 

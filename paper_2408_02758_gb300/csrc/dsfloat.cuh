@@ -88,13 +88,19 @@ __device__ __forceinline__ dsf tc() {
   return ds_make(TaylorCoef<K, PI>::h, TaylorCoef<K, PI>::l);
 }
 
-// Quarter-turn fix-up: (sin, cos) of (q * quarter + r) from (sin r, cos r), q taken mod 4.
+// Quarter-turn fix-up: (sin, cos) of (q * quarter + r) from (sin r, cos r), q taken mod 4: an odd
+// q swaps the pair, bit 1 of q negates the sine and bit 1 of q + 1 the cosine (selects and sign
+// flips, no branches).
+__device__ __forceinline__ dsf ds_flip(dsf a, unsigned int m) {
+  return ds_make(__uint_as_float(__float_as_uint(a.h) ^ m), __uint_as_float(__float_as_uint(a.l) ^ m));
+}
+
 __device__ __forceinline__ void ds_quadrant(int q, dsf sr, dsf cr, dsf& s, dsf& c) {
-  const int m = q & 3;
-  if (m == 0) { s = sr; c = cr; }
-  else if (m == 1) { s = cr; c = ds_neg(sr); }
-  else if (m == 2) { s = ds_neg(sr); c = ds_neg(cr); }
-  else { s = ds_neg(cr); c = sr; }
+  const bool odd = q & 1;
+  const dsf a = ds_make(odd ? cr.h : sr.h, odd ? cr.l : sr.l);
+  const dsf b = ds_make(odd ? sr.h : cr.h, odd ? sr.l : cr.l);
+  s = ds_flip(a, ((unsigned int)q << 30) & 0x80000000u);
+  c = ds_flip(b, ((unsigned int)(q + 1) << 30) & 0x80000000u);
 }
 
 // sin and cos of a tiny float-float x (|x| <= 0.025): the terms that matter at float-float

@@ -289,6 +289,22 @@ def test_float_float_readvection_matches_fp64_flowmap(F):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("preset,scale,kappa", [(1, 1 / 16, 0.01), (2, 1 / 8, 0.3)])
+def test_readvection_independent_of_lanes_per_block(F, preset, scale, kappa):
+    """How many nodes a block of the float-float re-advection takes (refine_lanes; the 2D double
+    gyre uses two lanes per node) changes scheduling only: results are bit-identical."""
+    w = I.preset(preset, scale=scale)
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    outs = []
+    for lanes in (32, 7, 1):
+        opt = F.make_options(refine_lanes=lanes, refine_kappa=kappa)  # a wide re-advection list
+        o = F.compute(dm, w.flow, w.T, w.dt, "fp32c", return_all=True, options=opt)
+        outs.append((o["ftle"].cpu().numpy(), F.flowmap_pairs(o["phi"], w.mesh.dim, w.mesh.n_nodes).cpu().numpy()))
+        assert F.ftle_read_counters(o["workspace"])["n_readvected"] > 0
+    for ft, ph in outs[1:]:
+        assert np.array_equal(ft, outs[0][0], equal_nan=True) and np.array_equal(ph, outs[0][1])
+
+
 @pytest.mark.parametrize("preset,scale,width", [(1, 1 / 16, None), (1, 1 / 16, 7), (2, 1 / 8, None), (0, 1 / 4, 4)])
 def test_fixed_width_neighbour_list_matches_csr(F, preset, scale, width):
     """The paper's fixed-width, -1 padded neighbour list gives bit-identical FTLE to the CSR rows
