@@ -35,12 +35,12 @@ FLUSH_BYTES = 320 << 20
 
 # Algorithmic FP32 flops of one compensated RK4 step per node (FMA = 2 flops; one sincospi or
 # sincos counted as 20 flops: argument reduction plus degree-7/8 minimax polynomials).
-#   double gyre: stage one 76 (error-free f 23, two sincospi 40, first-order corrections 10,
-#                velocity 3), per-step terms 8, stages two to four 3 x 46 (two small-angle
-#                rotations 30, the f difference 7, slope 4, increments 2, velocity 3), update 18
-#   ABC:         stage one 87 (three compensated sincos 78, velocity 9), stages two to four
-#                3 x 57 (three rotations 45, increments 3, velocity 9), update 27
-FLOPS_PER_POINT_STEP = {"dg": 240, "abc": 285}
+#   double gyre: stage one 74 (error-free f 17, two sincospi 40, first-order corrections 10,
+#                slope and velocity 7), per-step terms 6, stages two to four 3 x 43 (two
+#                small-angle rotations 30, angles 7, slope 2, increment 1, velocity 3), update 18
+#   ABC:         stage one 87 (three compensated sincos 78, increments 9), stages two to four
+#                3 x 54 (three rotations 45, increments 9), update 27
+FLOPS_PER_POINT_STEP = {"dg": 227, "abc": 276}
 
 
 def peak_fp32_tflops(sms: int, mhz: float) -> float:
