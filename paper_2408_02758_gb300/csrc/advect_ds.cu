@@ -145,29 +145,88 @@ __global__ void __launch_bounds__(32) k_advect_ds(AdvArgs a) {
 //   u = -pi A sin(pi f) cos(pi y),  v = pi A sin(pi y) cos(pi f) f_x,
 // and updates its own coordinate.  The node's two float-float chains run on two lanes instead of
 // interleaving in one, which halves the instructions a lane issues per stage; the arithmetic is
-// the single-lane kernel's up to the order of the velocity product.
+// the single-lane kernel's up to the order of the velocity product and of the final sum.
+struct DsPairConst {
+  dsf piA;              // -pi A on lane 0, pi A on lane 1
+  dsf h, h2, h6, third;
+  unsigned int mask;    // the two lanes of this pair
+  int p;
+};
+
+// whole_warp: every lane of the warp reaches each shuffle together (the single-problem kernel);
+// otherwise the shuffles name only the pair's two lanes.
+__device__ __forceinline__ DsPairConst ds_pair_const(const AdvArgs& a, bool whole_warp) {
+  DsPairConst K;
+  K.p = threadIdx.x & 1;
+  K.mask = whole_warp ? 0xffffffffu : 3u << (threadIdx.x & 30);
+  K.piA = ds_from_double((K.p ? kPi : -kPi) * a.p[0]);
+  K.h = ds_from_double(a.h);
+  K.h2 = ds_from_double(0.5 * a.h);
+  K.h6 = ds_from_double(a.h / 6.0);
+  K.third = ds_from_double(1.0 / 3.0);
+  return K;
+}
+
+// hc times this lane's velocity component at y, with a(t) = ca: the scale (a stage's step
+// fraction times -pi A or pi A times the partner's slope) is formed while the sine and cosine
+// evaluate, so two products follow them on the dependency chain.
+__device__ __forceinline__ dsf ds_pair_dg_vel(const DsPairConst& K, const dsf& y, const dsf& ca, const dsf& hc) {
+  const dsf ap = K.p ? ds_make(0.f, 0.f) : ca;
+  const dsf bp = K.p ? ds_make(1.0f, 0.0f) : ds_add_f(ds_make(-2.0f * ca.h, -2.0f * ca.l), 1.0f);
+  const dsf t1 = ds_mul(ap, y);
+  const dsf f = ds_mul(ds_add(t1, bp), y);
+  const dsf fx = ds_add(ds_make(2.0f * t1.h, 2.0f * t1.l), bp);
+  const dsf fq = ds_make(__shfl_xor_sync(K.mask, fx.h, 1), __shfl_xor_sync(K.mask, fx.l, 1));
+  const dsf g = ds_make(K.p ? fq.h : 1.0f, K.p ? fq.l : 0.0f);
+  const dsf scale = ds_mul(ds_mul(K.piA, g), hc);
+  dsf sn, cs;
+  ds_sincospi(f, sn, cs);
+  const dsf cq = ds_make(__shfl_xor_sync(K.mask, cs.h, 1), __shfl_xor_sync(K.mask, cs.l, 1));
+  return ds_mul(ds_mul(sn, cq), scale);
+}
+
+// One RK4 step of this lane's coordinate, with a(t) at the step's start, middle and end:
+// d1 = h/2 k1, d2 = h/2 k2, d3 = h k3, e4 = h/6 k4, and x + (d1 + 2 d2 + d3) / 3 + e4.
+__device__ __forceinline__ dsf ds_pair_dg_step(const DsPairConst& K, const dsf& x, const dsf& c0, const dsf& c1,
+                                               const dsf& c2) {
+  const dsf d1 = ds_pair_dg_vel(K, x, c0, K.h2);
+  const dsf d2 = ds_pair_dg_vel(K, ds_add(x, d1), c1, K.h2);
+  const dsf d3 = ds_pair_dg_vel(K, ds_add(x, d2), c1, K.h);
+  const dsf e4 = ds_pair_dg_vel(K, ds_add(x, d3), c2, K.h6);
+  const dsf sum = ds_add(ds_add(d1, d3), ds_make(2.0f * d2.h, 2.0f * d2.l));
+  return ds_add(x, ds_add(ds_mul(sum, K.third), e4));
+}
+
+// Lane 0 of a pair writes the node's gradient record (both coordinates, from the partner).
+__device__ __forceinline__ void ds_pair_store(const AdvArgs& a, const DsPairConst& K, int64_t i, bool active, float x0,
+                                              const dsf& x) {
+  const float q0 = __shfl_xor_sync(K.mask, x0, 1);
+  const float qh = __shfl_xor_sync(K.mask, x.h, 1), ql = __shfl_xor_sync(K.mask, x.l, 1);
+  if (!active) return;
+  reinterpret_cast<float2*>(a.out)[K.p * a.n_mesh + i] = make_float2(x.h, x.l);
+  if (a.rec && K.p == 0) {
+    const float xs[2] = {x0, q0}, ph[2] = {x.h, qh}, pl[2] = {x.l, ql};
+    store_record<2>(a.rec, i, xs, ph, pl);
+  }
+}
+
 template <typename CT>
 __global__ void __launch_bounds__(32) k_advect_ds_dg_pair(AdvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dsf* tab = reinterpret_cast<dsf*>(smem_raw);
   const int64_t count = a.list ? (int64_t)*a.list_count : a.n;
   const int nchunks = (a.nsteps + kAdvChunk - 1) / kAdvChunk;
-  const int p = threadIdx.x & 1;
-  const dsf piA = ds_from_double((p ? kPi : -kPi) * a.p[0]);
-  const dsf h = ds_from_double(a.h), h2 = ds_from_double(0.5 * a.h), h6 = ds_from_double(a.h / 6.0);
-  const dsf one = ds_make(1.0f, 0.0f);
-  const dsf third = ds_from_double(1.0 / 3.0);
+  const DsPairConst K = ds_pair_const(a, true);
   bool table_valid = false;
 
   const int lanes = (a.lanes > 0 && a.lanes < (int)blockDim.x) ? max(2, a.lanes & ~1) : (int)blockDim.x;
   const int per_block = lanes / 2;
   for (int64_t base = (int64_t)blockIdx.x * per_block; base < count; base += (int64_t)gridDim.x * per_block) {
     const int64_t slot = base + (threadIdx.x >> 1);
-    // both lanes of a pair are active or idle together; idle pairs integrate a dummy node so
-    // that every lane reaches each shuffle
+    // both lanes of a pair are active or idle together; idle pairs integrate a dummy node
     const bool active = (int)threadIdx.x < lanes && slot < count;
     const int64_t i = active ? (a.list ? (int64_t)a.list[slot] : slot) : 0;
-    dsf x = ds_from_double(active ? (double)__ldg(reinterpret_cast<const CT*>(a.coords) + p * a.n_mesh + i) : 0.0);
+    dsf x = ds_from_double(active ? (double)__ldg(reinterpret_cast<const CT*>(a.coords) + K.p * a.n_mesh + i) : 0.0);
     const float x0 = x.h;
     for (int ch = 0; ch < nchunks; ++ch) {
       const int k0 = ch * kAdvChunk;
@@ -179,44 +238,51 @@ __global__ void __launch_bounds__(32) k_advect_ds_dg_pair(AdvArgs a) {
         __syncthreads();
         table_valid = true;
       }
-      // hc times this lane's velocity component at y: the scale (a stage's step fraction times
-      // -pi A or pi A times the partner's slope) is formed while the sine and cosine evaluate, so
-      // two products follow them on the dependency chain
-      auto vel = [&](const dsf& y, const dsf& ca, const dsf& hc) -> dsf {
-        const dsf ap = p ? ds_make(0.f, 0.f) : ca;
-        const dsf bp = p ? one : ds_add_f(ds_make(-2.0f * ca.h, -2.0f * ca.l), 1.0f);
-        const dsf t1 = ds_mul(ap, y);
-        const dsf f = ds_mul(ds_add(t1, bp), y);
-        const dsf fx = ds_add(ds_make(2.0f * t1.h, 2.0f * t1.l), bp);
-        const dsf fq = ds_make(__shfl_xor_sync(0xffffffffu, fx.h, 1), __shfl_xor_sync(0xffffffffu, fx.l, 1));
-        const dsf g = ds_make(p ? fq.h : 1.0f, p ? fq.l : 0.0f);
-        const dsf scale = ds_mul(ds_mul(piA, g), hc);
-        dsf sn, cs;
-        ds_sincospi(f, sn, cs);
-        const dsf cq = ds_make(__shfl_xor_sync(0xffffffffu, cs.h, 1), __shfl_xor_sync(0xffffffffu, cs.l, 1));
-        return ds_mul(ds_mul(sn, cq), scale);
-      };
       for (int k = k0; k < k1; ++k) {
         const int m = 2 * (k - k0);
-        const dsf c0 = tab[m], c1 = tab[m + 1], c2 = tab[m + 2];
-        // d1 = h/2 k1, d2 = h/2 k2, d3 = h k3, e4 = h/6 k4; the step adds (d1 + 2 d2 + d3) / 3 + e4
-        const dsf d1 = vel(x, c0, h2);
-        const dsf d2 = vel(ds_add(x, d1), c1, h2);
-        const dsf d3 = vel(ds_add(x, d2), c1, h);
-        const dsf e4 = vel(ds_add(x, d3), c2, h6);
-        const dsf sum = ds_add(ds_add(d1, d3), ds_make(2.0f * d2.h, 2.0f * d2.l));
-        x = ds_add(x, ds_add(ds_mul(sum, third), e4));
+        x = ds_pair_dg_step(K, x, tab[m], tab[m + 1], tab[m + 2]);
       }
     }
-    const float q0 = __shfl_xor_sync(0xffffffffu, x0, 1);
-    const float qh = __shfl_xor_sync(0xffffffffu, x.h, 1), ql = __shfl_xor_sync(0xffffffffu, x.l, 1);
-    if (active) {
-      reinterpret_cast<float2*>(a.out)[p * a.n_mesh + i] = make_float2(x.h, x.l);
-      if (a.rec && p == 0) {
-        const float xs[2] = {x0, q0}, ph[2] = {x.h, qh}, pl[2] = {x.l, ql};
-        store_record<2>(a.rec, i, xs, ph, pl);
-      }
+    ds_pair_store(a, K, i, active, x0, x);
+  }
+}
+
+// Batched double-gyre re-advection on lane pairs: the list holds (instance, node) pairs, one per
+// lane pair, so pairs of one warp may belong to instances with different steps and parameters
+// (the shuffles name only the pair's two lanes).  Each pair forms its own coefficients
+// a(t_m) = eps sin(omega t_m) at the half steps t_m = t0 + m h/2 by turning (sin, cos)(omega t_m)
+// through the fixed angle omega h/2 with the angle-addition formulas in float-float: four
+// products and two sums per half step, off the state's dependency chain (rounding grows like
+// the square root of the half-step count, ~1e-13 relative after 3000 half steps).
+__global__ void __launch_bounds__(32) k_batch_advect_ds_dg_pair(const BatchInst* __restrict__ insts,
+                                                                const int2* pairs, const unsigned long long* count) {
+  const int64_t cnt = (int64_t)*count;
+  const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 1);
+  for (int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> 1) + (threadIdx.x >> 1); slot < cnt; slot += stride) {
+    const int2 pr = pairs[slot];
+    const AdvArgs& a = insts[pr.x].adv;
+    const int64_t i = pr.y;
+    const DsPairConst K = ds_pair_const(a, false);
+    const dsf eps = ds_from_double(a.p[1]);
+    const dsf rs = ds_from_double(sin(0.5 * a.p[2] * a.h)), rc = ds_from_double(cos(0.5 * a.p[2] * a.h));
+    dsf sw = ds_from_double(sin(a.p[2] * a.t0)), cw = ds_from_double(cos(a.p[2] * a.t0));
+    auto advance = [&]() {  // (sin, cos)(omega t) -> (sin, cos)(omega (t + h/2))
+      const dsf s2 = ds_add(ds_mul(sw, rc), ds_mul(cw, rs));
+      cw = ds_add(ds_mul(cw, rc), ds_neg(ds_mul(sw, rs)));
+      sw = s2;
+    };
+    dsf x = ds_from_double((double)__ldg(reinterpret_cast<const float*>(a.coords) + K.p * a.n_mesh + i));
+    const float x0 = x.h;
+    dsf c2 = ds_mul(eps, sw);
+    for (int k = 0; k < a.nsteps; ++k) {
+      const dsf c0 = c2;
+      advance();
+      const dsf c1 = ds_mul(eps, sw);
+      advance();
+      c2 = ds_mul(eps, sw);
+      x = ds_pair_dg_step(K, x, c0, c1, c2);
     }
+    ds_pair_store(a, K, i, true, x0, x);
   }
 }
 
@@ -290,7 +356,7 @@ __global__ void __launch_bounds__(32) k_batch_advect_ds(const BatchInst* __restr
 
 int launch_batch_advect_ds(int kind, int dim, const BatchInst* insts, const int2* pairs,
                            const unsigned long long* count, int grid, int block, cudaStream_t s) {
-  if (kind == FTLE_FLOW_DOUBLE_GYRE && dim == 2) k_batch_advect_ds<FTLE_FLOW_DOUBLE_GYRE, 2><<<grid, block, 0, s>>>(insts, pairs, count);
+  if (kind == FTLE_FLOW_DOUBLE_GYRE && dim == 2) k_batch_advect_ds_dg_pair<<<2 * grid, block, 0, s>>>(insts, pairs, count);
   else if (kind == FTLE_FLOW_ABC && dim == 3) k_batch_advect_ds<FTLE_FLOW_ABC, 3><<<grid, block, 0, s>>>(insts, pairs, count);
   else if (kind == FTLE_FLOW_LINEAR && dim == 2) k_batch_advect_ds<FTLE_FLOW_LINEAR, 2><<<grid, block, 0, s>>>(insts, pairs, count);
   else if (kind == FTLE_FLOW_LINEAR && dim == 3) k_batch_advect_ds<FTLE_FLOW_LINEAR, 3><<<grid, block, 0, s>>>(insts, pairs, count);
