@@ -137,9 +137,19 @@ __device__ __forceinline__ void store_record(float4* rec, int64_t i, const float
   }
 }
 
+// One 32-byte record in one 256-bit read-only load (records start 256-byte aligned and are 32
+// bytes each, so every record is 32-byte aligned): a warp reading consecutive records moves
+// whole lines in one instruction.
+__device__ __forceinline__ void ld_record256(const float4* p, float4& a, float4& b) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+
 template <int DIM>
 __device__ __forceinline__ void load_record(const float4* rec, int64_t i, float* x, float* ph, float* pl) {
-  const float4 a = __ldg(rec + 2 * i), b = __ldg(rec + 2 * i + 1);
+  float4 a, b;
+  ld_record256(rec + 2 * i, a, b);
   if constexpr (DIM == 2) {
     x[0] = a.x; x[1] = a.y; ph[0] = a.z; ph[1] = a.w; pl[0] = b.x; pl[1] = b.y;
   } else {

@@ -56,6 +56,38 @@ __device__ __forceinline__ T sym3_lmax(T a00, T a01, T a02, T a11, T a12, T a22,
   return q + T(2) * p * cos(acos(r) / T(3));
 }
 
+// Float variant of sym3_lmax for the float kernel: constant reciprocals and a reciprocal square
+// root instead of divisions, and c = cos(acos(r)/3) as the largest root of 4c^3 - 3c = r (the
+// triple-angle identity) by three Newton steps from c0 = 1/2 + sqrt((1 + r)/6), which lies above
+// that root for every r in [-1, 1], so the steps descend onto it.  Near r = -1 the root is double
+// and the steps slow down; such nodes (1 + r <= kNearDoubleTop) take the FP64 path anyway.
+__device__ __forceinline__ float sym3_lmax_f32(float a00, float a01, float a02, float a11, float a12, float a22,
+                                               float& r_out) {
+  const float q = (a00 + a11 + a22) * (1.0f / 3.0f);
+  const float p1 = fmaf(a01, a01, fmaf(a02, a02, a12 * a12));
+  const float d0 = a00 - q, d1 = a11 - q, d2 = a22 - q;
+  const float p2 = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, 2.0f * p1)));
+  if (!(p2 > 0.0f)) {
+    r_out = 1.0f;
+    return q;
+  }
+  const float pp = p2 * (1.0f / 6.0f);  // p^2
+  const float rp = rsqrtf(pp);          // 1 / p
+  const float p = pp * rp;
+  const float det = d0 * (d1 * d2 - a12 * a12) - a01 * (a01 * d2 - a12 * a02) + a02 * (a01 * a12 - d1 * a02);
+  float r = 0.5f * det * (rp * rp * rp);
+  r = fminf(fmaxf(r, -1.0f), 1.0f);
+  r_out = r;
+  float c = 0.5f + sqrtf((1.0f + r) * (1.0f / 6.0f));
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    const float c2 = c * c;
+    const float g = fmaf(c, fmaf(4.0f, c2, -3.0f), -r);
+    c -= __fdividef(g, fmaf(12.0f, c2, -3.0f));
+  }
+  return fmaf(2.0f * p, c, q);
+}
+
 // M += dx dx^T (upper triangle), B += dphi dx^T.
 template <int DIM>
 __device__ __forceinline__ void grad_moments(const float* dx, const float* dp, float* m, float* b) {
@@ -146,7 +178,7 @@ __device__ __forceinline__ bool grad_finish_f32(const GradArgs& a, int64_t i, in
     if (!(det > kCondFlag * tr3 * tr3 * tr3)) {
       flag = true;
     } else {
-      const float inv = 1.0f / det;
+      const float inv = __fdividef(1.0f, det);  // det > 0 here; a reciprocal to ~2 ulp
       float F[9];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
@@ -163,15 +195,18 @@ __device__ __forceinline__ bool grad_finish_f32(const GradArgs& a, int64_t i, in
         for (int s = r; s < 3; ++s)
           c[q++] = fmaf(F[r], F[s], fmaf(F[3 + r], F[3 + s], F[6 + r] * F[6 + s]));
       float rr;
-      lam = sym3_lmax<float>(c[0], c[1], c[2], c[3], c[4], c[5], rr);
+      lam = sym3_lmax_f32(c[0], c[1], c[2], c[3], c[4], c[5], rr);
       if (rr <= -1.0f + kNearDoubleTop) flag = true;
     }
   }
   mu = lam - 1.0f;
-  const float h_i = sqrtf(trm / (float)(k > 0 ? k : 1));
-  const bool sensitive = (a.refine_kappa >= 0.f) && !(log1pf(mu) * h_i >= a.refine_kappa);
+  // ln(lambda_max) h_i < kappa with h_i = sqrt(tr M / k), compared squared (mu < kMuFloor, where
+  // the log could be negative, is flagged anyway)
+  const float lg = log1pf(mu);
+  const bool sensitive =
+      (a.refine_kappa >= 0.f) && !(lg * lg * trm >= a.refine_kappa * a.refine_kappa * (float)k);
   flag = flag || !(mu >= kMuFloor) || sensitive || !(lam == lam);
-  const float ftle = flag ? NAN : log1pf(mu) * (float)a.inv_2absT;
+  const float ftle = flag ? NAN : lg * (float)a.inv_2absT;
   reinterpret_cast<float*>(a.ftle_out)[i] = ftle;
   if (a.lam_out) a.lam_out[i] = flag ? NAN : (double)lam;
   return flag;
@@ -238,12 +273,13 @@ __device__ __forceinline__ bool grad_node_f32_ell_rec(const GradArgs& a, int64_t
   load_record<DIM>(a.rec, i, xi, hi, li);
   int k = 0;
   if constexpr (W > 0) {
+    // an absent neighbour (-1) reads the node's own record: dx = dphi = 0 leaves the sums
+    // unchanged exactly, and the loop has no branch
 #pragma unroll
     for (int s = 0; s < W; ++s) {
-      if (js[s] >= 0) {
-        grad_accumulate_rec<DIM>(a.rec, js[s], xi, hi, li, m, b);
-        ++k;
-      }
+      const bool ok = js[s] >= 0;
+      grad_accumulate_rec<DIM>(a.rec, (uint32_t)(ok ? js[s] : (int)i), xi, hi, li, m, b);
+      k += ok;
     }
   } else {
     for (int s = 0; s < a.ell_width; ++s) {
