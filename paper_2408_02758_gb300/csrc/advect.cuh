@@ -178,52 +178,75 @@ __device__ __forceinline__ void comp_add(float xh, float d, float& s, float& e) 
 //   f_s(x0 + dx) - f_0(x0) = dx (1 + a_s (2 (x0 - 1) + dx)) + (a_s - a_0) x0 (x0 - 2),
 // a small difference that float forms to a relative rounding (e1 = 2 (x0 - 1), dg = the last
 // term).  The stage's (sin, cos)(pi f) and (sin, cos)(pi y) are stage one's pairs rotated by pi
-// times the differences; a lane whose angle exceeds kRotMax evaluates the stage in full at the
-// compensated stage point instead.  Returns the velocity without its factors -pi A and pi A.
-// The y increment arrives as kv with two scales: hy (dy = hy kv) and hy_pi (the angle pi dy).
-__device__ __forceinline__ void dg_stage_rot(const Coef& cs, float e1, float dg, float dx, float kv_prev, float hy,
-                                             float hy_pi, float sf, float cf, float sy, float cy, const float* xh,
-                                             const float* xl, float& ku, float& kv) {
+// times the differences.  The larger angle joins `mx`; a step whose largest angle exceeds
+// kRotMax is recomputed in full (rk4_step_c_full).  The y increment arrives as kv with the
+// angle's scale hy_pi (pi times the increment's scale).  Returns the velocity without its
+// factors -pi A and pi A.
+__device__ __forceinline__ void dg_stage_rot(float as, float e1, float dg, float dx, float kv_prev, float hy_pi,
+                                             float sf, float cf, float sy, float cy, float& mx, float& ku,
+                                             float& kv) {
   const float kPiF = 3.14159265358979323846f;
-  const float w = fmaf(cs.a, e1 + dx, 1.0f);  // 1 + a_s (2 (x0 - 1) + dx)
+  const float w = fmaf(as, e1 + dx, 1.0f);  // 1 + a_s (2 (x0 - 1) + dx)
   const float tf = kPiF * fmaf(dx, w, dg);
   const float ty = hy_pi * kv_prev;
-  float sfs, cfs, sys, cys, fxs;
-  if (fmaxf(fabsf(tf), fabsf(ty)) <= kRotMax) {
-    rotate_small(sf, cf, tf, sfs, cfs);
-    rotate_small(sy, cy, ty, sys, cys);
-    fxs = fmaf(cs.a, dx, w);  // f_s'(x0 + dx) = 1 + 2 a_s (x0 + dx - 1)
-  } else {
-    float ph, pe, qh, qe;
-    two_sum(xh[0], dx, ph, pe);
-    two_sum(xh[1], hy * kv_prev, qh, qe);
-    dg_base32c(cs.a, cs.bh, cs.bl, ph, pe + xl[0], qh, qe + xl[1], sfs, cfs, sys, cys, fxs);
-  }
+  mx = fmaxf(mx, fmaxf(fabsf(tf), fabsf(ty)));
+  float sfs, cfs, sys, cys;
+  rotate_small(sf, cf, tf, sfs, cfs);
+  rotate_small(sy, cy, ty, sys, cys);
+  const float fxs = fmaf(as, dx, w);  // f_s'(x0 + dx) = 1 + 2 a_s (x0 + dx - 1)
   ku = sfs * cys;
   kv = cfs * sys * fxs;
 }
 
 // ABC stage two, three or four of the compensated step: stage one's (sin, cos) of x, y, z rotated
-// by the stage increments d (radians); full evaluation at the compensated stage point when an
-// increment exceeds kRotMax.
+// by the stage increments d (radians); the largest increment joins `mx`.  co = (A, B, C) times
+// the scale of the value returned (the next stage's increment, or h/6 k4).
 __device__ __forceinline__ void abc_stage_rot(const float* co, const float* d, const float* s0, const float* c0,
-                                              const float* xh, const float* xl, float* k) {
+                                              float& mx, float* k) {
   float s[3], c[3];
-  if (fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))) <= kRotMax) {
+  mx = fmaxf(mx, fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))));
 #pragma unroll
-    for (int q = 0; q < 3; ++q) rotate_small(s0[q], c0[q], d[q], s[q], c[q]);
-  } else {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      float ph, pe;
-      two_sum(xh[q], d[q], ph, pe);
-      fsincos_c(ph, pe + xl[q], s[q], c[q]);
-    }
-  }
-  // co = (A, B, C) times the scale of the value returned (the next stage's increment, or h/6)
+  for (int q = 0; q < 3; ++q) rotate_small(s0[q], c0[q], d[q], s[q], c[q]);
   k[0] = fmaf(co[0], s[2], co[2] * c[1]);
   k[1] = fmaf(co[1], s[0], co[0] * c[2]);
   k[2] = fmaf(co[2], s[1], co[1] * c[0]);
+}
+
+// One RK4 step of the compensated state with every stage's velocity evaluated in full at the
+// compensated stage point (flows without a rotated form, and steps too long for the rotation).
+template <int KIND, int DIM>
+__device__ __forceinline__ void rk4_step_c_full(const AdvArgs& a, const Coef& c0, const Coef& c1, const Coef& c2,
+                                                float* xh, float* xl) {
+  float k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], yh[DIM], yl[DIM];
+  vel_f32c<KIND, DIM>(a, xh, xl, c0.a, c0.bh, c0.bl, k1v);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    float e;
+    comp_add<KIND>(xh[d], a.h2_32 * k1v[d], yh[d], e);
+    yl[d] = e + xl[d];
+  }
+  vel_f32c<KIND, DIM>(a, yh, yl, c1.a, c1.bh, c1.bl, k2v);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    float e;
+    comp_add<KIND>(xh[d], a.h2_32 * k2v[d], yh[d], e);
+    yl[d] = e + xl[d];
+  }
+  vel_f32c<KIND, DIM>(a, yh, yl, c1.a, c1.bh, c1.bl, k3v);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    float e;
+    comp_add<KIND>(xh[d], a.h32 * k3v[d], yh[d], e);
+    yl[d] = e + xl[d];
+  }
+  vel_f32c<KIND, DIM>(a, yh, yl, c2.a, c2.bh, c2.bl, k4v);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    float s, e;
+    comp_add<KIND>(xh[d], fmaf(a.h6_32, fmaf(2.f, k2v[d] + k3v[d], k1v[d] + k4v[d]), xl[d]), s, e);
+    xh[d] = s;
+    xl[d] = e;
+  }
 }
 
 // Advance one node by one classic RK4 step (stages at t, t + h/2, t + h/2, t + h, with the
@@ -268,70 +291,49 @@ __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const
     const float k1u = sf * cy, k1v = cf * sy * fx;
     const float g0 = xh[0] * (xh[0] - 2.0f);
     const float dg1 = (c1.a - c0.a) * g0, dg2 = (c2.a - c0.a) * g0;
-    float k2u, k2v, k3u, k3v, k4u, k4v;
-    dg_stage_rot(c1, e1, dg1, a.hs[0][0] * k1u, k1v, a.hs[1][0], a.hs_pi[0], sf, cf, sy, cy, xh, xl, k2u, k2v);
-    dg_stage_rot(c1, e1, dg1, a.hs[0][0] * k2u, k2v, a.hs[1][0], a.hs_pi[0], sf, cf, sy, cy, xh, xl, k3u, k3v);
-    dg_stage_rot(c2, e1, dg2, a.hs[0][1] * k3u, k3v, a.hs[1][1], a.hs_pi[1], sf, cf, sy, cy, xh, xl, k4u, k4v);
-    const float inc[2] = {a.hs[0][2] * fmaf(2.f, k2u + k3u, k1u + k4u), a.hs[1][2] * fmaf(2.f, k2v + k3v, k1v + k4v)};
+    float k2u, k2v, k3u, k3v, k4u, k4v, mx = 0.0f;
+    dg_stage_rot(c1.a, e1, dg1, a.hs[0][0] * k1u, k1v, a.hs_pi[0], sf, cf, sy, cy, mx, k2u, k2v);
+    dg_stage_rot(c1.a, e1, dg1, a.hs[0][0] * k2u, k2v, a.hs_pi[0], sf, cf, sy, cy, mx, k3u, k3v);
+    dg_stage_rot(c2.a, e1, dg2, a.hs[0][1] * k3u, k3v, a.hs_pi[1], sf, cf, sy, cy, mx, k4u, k4v);
+    if (mx <= kRotMax) {
+      // the increment h/6 (k1 + 2 k2 + 2 k3 + k4) and the low part join in one rounding
+      const float sum[2] = {fmaf(2.f, k2u + k3u, k1u + k4u), fmaf(2.f, k2v + k3v, k1v + k4v)};
 #pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      float s, e;
-      comp_add<KIND>(xh[d], inc[d] + xl[d], s, e);
-      xh[d] = s;
-      xl[d] = e;
+      for (int d = 0; d < 2; ++d) {
+        float s, e;
+        comp_add<KIND>(xh[d], fmaf(a.hs[d][2], sum[d], xl[d]), s, e);
+        xh[d] = s;
+        xl[d] = e;
+      }
+    } else {
+      rk4_step_c_full<KIND, DIM>(a, c0, c1, c2, xh, xl);
     }
   } else if constexpr (KIND == FTLE_FLOW_ABC) {  // P32C, stages two to four by rotation
     // stage increments d1 = h/2 k1, d2 = h/2 k2, d3 = h k3 and e4 = h/6 k4 straight from the
     // folded constants; the step adds (d1 + 2 d2 + d3) / 3 + e4 = h/6 (k1 + 2 k2 + 2 k3 + k4)
-    float s0[3], c0v[3], d1[3], d2[3], d3[3], e4[3];
+    float s0[3], c0v[3], d1[3], d2[3], d3[3], e4[3], mx = 0.0f;
 #pragma unroll
     for (int q = 0; q < 3; ++q) fsincos_c(xh[q], xl[q], s0[q], c0v[q]);
     d1[0] = fmaf(a.habc[0][0], s0[2], a.habc[0][2] * c0v[1]);
     d1[1] = fmaf(a.habc[0][1], s0[0], a.habc[0][0] * c0v[2]);
     d1[2] = fmaf(a.habc[0][2], s0[1], a.habc[0][1] * c0v[0]);
-    abc_stage_rot(a.habc[0], d1, s0, c0v, xh, xl, d2);
-    abc_stage_rot(a.habc[1], d2, s0, c0v, xh, xl, d3);
-    abc_stage_rot(a.habc[2], d3, s0, c0v, xh, xl, e4);
+    abc_stage_rot(a.habc[0], d1, s0, c0v, mx, d2);
+    abc_stage_rot(a.habc[1], d2, s0, c0v, mx, d3);
+    abc_stage_rot(a.habc[2], d3, s0, c0v, mx, e4);
+    if (mx <= kRotMax) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float inc = fmaf(fmaf(2.f, d2[q], d1[q] + d3[q]), 1.0f / 3.0f, e4[q]);
-      float s, e;
-      comp_add<KIND>(xh[q], inc + xl[q], s, e);
-      xh[q] = s;
-      xl[q] = e;
+      for (int q = 0; q < 3; ++q) {
+        const float inc = fmaf(fmaf(2.f, d2[q], d1[q] + d3[q]), 1.0f / 3.0f, e4[q]);
+        float s, e;
+        comp_add<KIND>(xh[q], inc + xl[q], s, e);
+        xh[q] = s;
+        xl[q] = e;
+      }
+    } else {
+      rk4_step_c_full<KIND, DIM>(a, c0, c1, c2, xh, xl);
     }
   } else {  // P32C, other flows: velocity at the compensated stage points
-    float k1v[DIM], k2v[DIM], k3v[DIM], k4v[DIM], yh[DIM], yl[DIM];
-    vel_f32c<KIND, DIM>(a, xh, xl, c0.a, c0.bh, c0.bl, k1v);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      float e;
-      comp_add<KIND>(xh[d], a.h2_32 * k1v[d], yh[d], e);
-      yl[d] = e + xl[d];
-    }
-    vel_f32c<KIND, DIM>(a, yh, yl, c1.a, c1.bh, c1.bl, k2v);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      float e;
-      comp_add<KIND>(xh[d], a.h2_32 * k2v[d], yh[d], e);
-      yl[d] = e + xl[d];
-    }
-    vel_f32c<KIND, DIM>(a, yh, yl, c1.a, c1.bh, c1.bl, k3v);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      float e;
-      comp_add<KIND>(xh[d], a.h32 * k3v[d], yh[d], e);
-      yl[d] = e + xl[d];
-    }
-    vel_f32c<KIND, DIM>(a, yh, yl, c2.a, c2.bh, c2.bl, k4v);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      const float inc = a.h6_32 * fmaf(2.f, k2v[d] + k3v[d], k1v[d] + k4v[d]);
-      float s, e;
-      comp_add<KIND>(xh[d], inc + xl[d], s, e);
-      xh[d] = s;
-      xl[d] = e;
-    }
+    rk4_step_c_full<KIND, DIM>(a, c0, c1, c2, xh, xl);
   }
 }
 
