@@ -31,9 +31,9 @@ __device__ __forceinline__ void vel_ds(const DsFlow& F, const dsf* x, dsf a, dsf
     ds_sincos(x[0], sx, cx);
     ds_sincos(x[1], sy, cy);
     ds_sincos(x[2], sz, cz);
-    u[0] = ds_add(ds_mul(F.c[0], sz), ds_mul(F.c[2], cy));
-    u[1] = ds_add(ds_mul(F.c[1], sx), ds_mul(F.c[0], cz));
-    u[2] = ds_add(ds_mul(F.c[2], sy), ds_mul(F.c[1], cx));
+    u[0] = ds_add(ds_mul_u(F.c[0], sz), ds_mul_u(F.c[2], cy));
+    u[1] = ds_add(ds_mul_u(F.c[1], sx), ds_mul_u(F.c[0], cz));
+    u[2] = ds_add(ds_mul_u(F.c[2], sy), ds_mul_u(F.c[1], cx));
   } else if constexpr (KIND == FTLE_FLOW_LINEAR) {
 #pragma unroll
     for (int r = 0; r < DIM; ++r) {
@@ -52,7 +52,7 @@ __device__ __forceinline__ void vel_ds(const DsFlow& F, const dsf* x, dsf a, dsf
 template <int DIM>
 __device__ __forceinline__ void ds_axpy(const dsf* x, dsf h, const dsf* k, dsf* y) {
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) y[d] = ds_add(x[d], ds_mul(h, k[d]));
+  for (int d = 0; d < DIM; ++d) y[d] = ds_add(x[d], ds_mul_u(h, k[d]));
 }
 
 template <int KIND, int DIM, typename CT>
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(32) k_advect_ds(AdvArgs a) {
         for (int d = 0; d < DIM; ++d) {
           const dsf s23 = ds_add(k2v[d], k3v[d]);
           const dsf s = ds_add(ds_add(k1v[d], k4v[d]), ds_make(2.0f * s23.h, 2.0f * s23.l));
-          x[d] = ds_add(x[d], ds_mul(h6, s));
+          x[d] = ds_add(x[d], ds_mul_u(h6, s));
         }
       }
     }
@@ -173,8 +173,8 @@ __device__ __forceinline__ DsPairConst ds_pair_const(const AdvArgs& a, bool whol
 __device__ __forceinline__ dsf ds_pair_dg_vel(const DsPairConst& K, const dsf& y, const dsf& ca, const dsf& hc) {
   const dsf ap = K.p ? ds_make(0.f, 0.f) : ca;
   const dsf bp = K.p ? ds_make(1.0f, 0.0f) : ds_add_f(ds_make(-2.0f * ca.h, -2.0f * ca.l), 1.0f);
-  const dsf t1 = ds_mul(ap, y);
-  const dsf f = ds_mul(ds_add(t1, bp), y);
+  const dsf t1 = ds_mul_u(ap, y);
+  const dsf f = ds_mul(ds_add(t1, bp), y);  // normalized: its high part is reduced by rint
   const dsf fx = ds_add(ds_make(2.0f * t1.h, 2.0f * t1.l), bp);
   const dsf fq = ds_make(__shfl_xor_sync(K.mask, fx.h, 1), __shfl_xor_sync(K.mask, fx.l, 1));
   const dsf g = ds_make(K.p ? fq.h : 1.0f, K.p ? fq.l : 0.0f);
@@ -182,7 +182,7 @@ __device__ __forceinline__ dsf ds_pair_dg_vel(const DsPairConst& K, const dsf& y
   dsf sn, cs;
   ds_sincospi(f, sn, cs);
   const dsf cq = ds_make(__shfl_xor_sync(K.mask, cs.h, 1), __shfl_xor_sync(K.mask, cs.l, 1));
-  return ds_mul(ds_mul(sn, cq), scale);
+  return ds_mul_u(ds_mul_u(sn, cq), scale);
 }
 
 // One RK4 step of this lane's coordinate, with a(t) at the step's start, middle and end:
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(32) k_batch_advect_ds(const BatchInst* __restr
       for (int d = 0; d < DIM; ++d) {
         const dsf s23 = ds_add(k2v[d], k3v[d]);
         const dsf s = ds_add(ds_add(k1v[d], k4v[d]), ds_make(2.0f * s23.h, 2.0f * s23.l));
-        x[d] = ds_add(x[d], ds_mul(h6, s));
+        x[d] = ds_add(x[d], ds_mul_u(h6, s));
       }
     }
     float2* o = reinterpret_cast<float2*>(a.out);

@@ -49,6 +49,17 @@ __device__ __forceinline__ dsf ds_mul(dsf a, dsf b) {
   return ds_fast(p, e);
 }
 
+// Product without the final renormalization: (p, e) with p = fl(a.h b.h) and e the rest to
+// first order, |e| within a couple of ulps of p.  For operands of another product or of a sum,
+// which take the pair as it is; it saves the Fast2Sum's three dependent operations on the chain.
+__device__ __forceinline__ dsf ds_mul_u(dsf a, dsf b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return ds_make(p, e);
+}
+
 __device__ __forceinline__ dsf ds_mul_f(dsf a, float b) {
   const float p = __fmul_rn(a.h, b);
   float e = fmaf(a.h, b, -p);
@@ -106,21 +117,21 @@ __device__ __forceinline__ void ds_quadrant(int q, dsf sr, dsf cr, dsf& s, dsf& 
 // sin and cos of a tiny float-float x (|x| <= 0.025): the terms that matter at float-float
 // precision (x, x^3/6, x^2/2) in float-float, the small remainder of each series in float.
 __device__ __forceinline__ void ds_sincos_tiny(dsf x, dsf& s, dsf& c) {
-  const dsf x2 = ds_mul(x, x);
+  const dsf x2 = ds_mul_u(x, x);
   // sin x = x + x^3 (-1/6 + x^2/120 - x^4/5040)
   const float q = x2.h * fmaf(-x2.h, 1.0f / 5040.0f, 1.0f / 120.0f);
   const dsf cs = ds_add_f(tc<3, false>(), q);
-  s = ds_add(x, ds_mul(ds_mul(x2, x), cs));
+  s = ds_add(x, ds_mul_u(ds_mul_u(x2, x), cs));
   // cos x = 1 + x^2 (-1/2 + x^2/24 - x^4/720)
   const float p = x2.h * fmaf(-x2.h, 1.0f / 720.0f, 1.0f / 24.0f);
-  c = ds_add_f(ds_mul(x2, ds_add_f(ds_make(-0.5f, 0.f), p)), 1.0f);
+  c = ds_add_f(ds_mul_u(x2, ds_add_f(ds_make(-0.5f, 0.f), p)), 1.0f);
 }
 
 // (sin, cos)(a + u) from the tabulated (sin, cos)(a) and the tiny-argument pair of u.
 __device__ __forceinline__ void ds_rotate(const float4 t, dsf su, dsf cu, dsf& s, dsf& c) {
   const dsf sa = ds_make(t.x, t.y), ca = ds_make(t.z, t.w);
-  s = ds_add(ds_mul(sa, cu), ds_mul(ca, su));
-  c = ds_add(ds_mul(ca, cu), ds_neg(ds_mul(sa, su)));
+  s = ds_add(ds_mul_u(sa, cu), ds_mul_u(ca, su));
+  c = ds_add(ds_mul_u(ca, cu), ds_neg(ds_mul_u(sa, su)));
 }
 
 // sin(pi x), cos(pi x) of a float-float x: x = k/2 + r (|r| <= 1/4), r = j/64 + u (|u| <= 1/128),
@@ -131,7 +142,7 @@ __device__ __forceinline__ void ds_sincospi(dsf x, dsf& s, dsf& c) {
   const float j = rintf(64.0f * r.h);
   const dsf u = ds_fast(r.h - j * (1.0f / 64.0f), r.l);
   dsf su, cu, sr, cr;
-  ds_sincos_tiny(ds_mul(u, tc<1, true>()), su, cu);
+  ds_sincos_tiny(ds_mul_u(u, tc<1, true>()), su, cu);
   ds_rotate(__ldg(reinterpret_cast<const float4*>(kDS_SINPI_TAB) + (int)j + 16), su, cu, sr, cr);
   ds_quadrant((int)k, sr, cr, s, c);
 }
