@@ -174,7 +174,7 @@ __device__ __forceinline__ dsf ds_pair_dg_vel(const DsPairConst& K, const dsf& y
   const dsf ap = K.p ? ds_make(0.f, 0.f) : ca;
   const dsf bp = K.p ? ds_make(1.0f, 0.0f) : ds_add_f(ds_make(-2.0f * ca.h, -2.0f * ca.l), 1.0f);
   const dsf t1 = ds_mul_u(ap, y);
-  const dsf f = ds_mul(ds_add(t1, bp), y);  // normalized: its high part is reduced by rint
+  const dsf f = ds_mul(ds_add_u(t1, bp), y);  // normalized: its high part is reduced by rint
   const dsf fx = ds_add(ds_make(2.0f * t1.h, 2.0f * t1.l), bp);
   const dsf fq = ds_make(__shfl_xor_sync(K.mask, fx.h, 1), __shfl_xor_sync(K.mask, fx.l, 1));
   const dsf g = ds_make(K.p ? fq.h : 1.0f, K.p ? fq.l : 0.0f);
@@ -190,9 +190,9 @@ __device__ __forceinline__ dsf ds_pair_dg_vel(const DsPairConst& K, const dsf& y
 __device__ __forceinline__ dsf ds_pair_dg_step(const DsPairConst& K, const dsf& x, const dsf& c0, const dsf& c1,
                                                const dsf& c2) {
   const dsf d1 = ds_pair_dg_vel(K, x, c0, K.h2);
-  const dsf d2 = ds_pair_dg_vel(K, ds_add(x, d1), c1, K.h2);
-  const dsf d3 = ds_pair_dg_vel(K, ds_add(x, d2), c1, K.h);
-  const dsf e4 = ds_pair_dg_vel(K, ds_add(x, d3), c2, K.h6);
+  const dsf d2 = ds_pair_dg_vel(K, ds_add_u(x, d1), c1, K.h2);
+  const dsf d3 = ds_pair_dg_vel(K, ds_add_u(x, d2), c1, K.h);
+  const dsf e4 = ds_pair_dg_vel(K, ds_add_u(x, d3), c2, K.h6);
   const dsf sum = ds_add(ds_add(d1, d3), ds_make(2.0f * d2.h, 2.0f * d2.l));
   return ds_add(x, ds_add(ds_mul(sum, K.third), e4));
 }

@@ -34,6 +34,14 @@ __device__ __forceinline__ dsf ds_add(dsf a, dsf b) {
   return ds_fast(s, e);
 }
 
+// Sum without the final renormalization, for operands of a product or of another sum whose terms
+// do not cancel (|a + b| not far below |a| + |b|): the pair (s, e), |e| within a few ulps of s.
+__device__ __forceinline__ dsf ds_add_u(dsf a, dsf b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return ds_make(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+
 __device__ __forceinline__ dsf ds_add_f(dsf a, float b) {
   float s, e;
   two_sum(a.h, b, s, e);
@@ -121,7 +129,7 @@ __device__ __forceinline__ void ds_sincos_tiny(dsf x, dsf& s, dsf& c) {
   // sin x = x + x^3 (-1/6 + x^2/120 - x^4/5040)
   const float q = x2.h * fmaf(-x2.h, 1.0f / 5040.0f, 1.0f / 120.0f);
   const dsf cs = ds_add_f(tc<3, false>(), q);
-  s = ds_add(x, ds_mul_u(ds_mul_u(x2, x), cs));
+  s = ds_add_u(x, ds_mul_u(ds_mul_u(x2, x), cs));
   // cos x = 1 + x^2 (-1/2 + x^2/24 - x^4/720)
   const float p = x2.h * fmaf(-x2.h, 1.0f / 720.0f, 1.0f / 24.0f);
   c = ds_add_f(ds_mul_u(x2, ds_add_f(ds_make(-0.5f, 0.f), p)), 1.0f);
@@ -130,8 +138,8 @@ __device__ __forceinline__ void ds_sincos_tiny(dsf x, dsf& s, dsf& c) {
 // (sin, cos)(a + u) from the tabulated (sin, cos)(a) and the tiny-argument pair of u.
 __device__ __forceinline__ void ds_rotate(const float4 t, dsf su, dsf cu, dsf& s, dsf& c) {
   const dsf sa = ds_make(t.x, t.y), ca = ds_make(t.z, t.w);
-  s = ds_add(ds_mul_u(sa, cu), ds_mul_u(ca, su));
-  c = ds_add(ds_mul_u(ca, cu), ds_neg(ds_mul_u(sa, su)));
+  s = ds_add_u(ds_mul_u(sa, cu), ds_mul_u(ca, su));
+  c = ds_add_u(ds_mul_u(ca, cu), ds_neg(ds_mul_u(sa, su)));
 }
 
 // sin(pi x), cos(pi x) of a float-float x: x = k/2 + r (|r| <= 1/4), r = j/64 + u (|u| <= 1/128),
