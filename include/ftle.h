@@ -134,7 +134,11 @@ typedef struct ftle_options {
 /* Bytes of a flowmap buffer for `precision` (0 on bad arguments).  For FP32C the buffer holds the
  * (hi, lo) pairs float2 [dim][n] followed, at the next 256-byte boundary, by one 32-byte record
  * per node that the float gradient kernel reads (coordinates, hi parts and low parts packed:
- * 2D {x, y, hx, hy}{lx, ly, 0, 0}; 3D {x, y, z, hx}{hy, hz, lx, bf16(ly) | bf16(lz) << 16}). */
+ * 2D {x, y, hx, hy}{lx, ly, 0, 0}; 3D {x, y, z, hx}{hy, hz, lx, bf16(ly) | bf16(lz) << 16}).
+ * A 2D FP32C flowmap then holds, each at the next 256-byte boundary, 7 more (hi, lo) states
+ * float2 [2][n]: slot j is the state after min((j + 1) L, nsteps) steps, L = ceil(nsteps / 8),
+ * the starting points from which ftle_refine re-advects 8 runs of a node side by side.
+ * ftle_refine therefore takes the flowmap ftle_advect wrote with the same t0, T and dt. */
 size_t ftle_flowmap_bytes(int32_t dim, int64_t n_nodes, int32_t precision);
 
 /* Bytes of one checkpoint slot: the state alone (the FP32C (hi, lo) pairs, without records). */

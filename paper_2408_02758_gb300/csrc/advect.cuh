@@ -33,6 +33,9 @@ struct AdvArgs {
   const unsigned long long* list_count;
   int lanes;                   // active threads per block (0 = all): few-node lists spread wider
   float4* rec;                 // nullable: gradient records of a compensated flowmap
+  float2* seg;                 // nullable: run-boundary states of a compensated 2D flowmap
+  int64_t seg_stride;          // float2 per boundary slot
+  int seg_len;                 // steps per run
 };
 
 // ------------------------------------------------------------------------- velocity dispatch
@@ -395,6 +398,8 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
     if (a.ckpt && active) store_state<OUT, DIM>(a.ckpt, a.n_mesh, i, xh, xl, xd);
     int ck_left = a.ckpt_every;
     int ck_slot = 1;
+    constexpr bool kSegs = PREC == P32C && OUT == O32PAIR && DIM == 2;
+    int seg_slot = 0, next_seg = a.seg_len;
 
     for (int ch = 0; ch < nchunks; ++ch) {
       const int k0 = ch * kAdvChunk;
@@ -408,22 +413,40 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
         }
       }
       if (!active) continue;
-      for (int k = k0; k < k1; ++k) {
-        const int m = 2 * (k - k0);
-        const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
-        const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
-        const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
-        rk4_step<KIND, DIM, PREC>(a, c0, c1, c2, xh, xl, xd);
-        if (a.ckpt) {
-          if (--ck_left == 0) {
-            ck_left = a.ckpt_every;
-            split_state<PREC, DIM>(xh, xl, xd);
-            store_state<OUT, DIM>(reinterpret_cast<char*>(a.ckpt) + (int64_t)ck_slot * a.ckpt_stride_bytes,
-                                  a.n_mesh, i, xh, xl, xd);
-            ++ck_slot;
+      for (int k = k0; k < k1;) {
+        // steps up to the next run boundary (uniform across the block), then its state
+        const int stop = (kSegs && a.seg) ? min(k1, next_seg) : k1;
+        for (; k < stop; ++k) {
+          const int m = 2 * (k - k0);
+          const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
+          const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
+          const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
+          rk4_step<KIND, DIM, PREC>(a, c0, c1, c2, xh, xl, xd);
+          if (a.ckpt) {
+            if (--ck_left == 0) {
+              ck_left = a.ckpt_every;
+              split_state<PREC, DIM>(xh, xl, xd);
+              store_state<OUT, DIM>(reinterpret_cast<char*>(a.ckpt) + (int64_t)ck_slot * a.ckpt_stride_bytes,
+                                    a.n_mesh, i, xh, xl, xd);
+              ++ck_slot;
+            }
+          }
+        }
+        if constexpr (kSegs) {
+          if (a.seg && k == next_seg) {
+            if (seg_slot < kSegments - 1)
+              store_state<OUT, DIM>(a.seg + (int64_t)seg_slot * a.seg_stride, a.n_mesh, i, xh, xl, xd);
+            ++seg_slot;
+            next_seg += a.seg_len;
           }
         }
       }
+    }
+    if constexpr (kSegs) {
+      // boundaries at or past the last step hold the final state
+      if (a.seg && active)
+        for (; seg_slot < kSegments - 1; ++seg_slot)
+          store_state<OUT, DIM>(a.seg + (int64_t)seg_slot * a.seg_stride, a.n_mesh, i, xh, xl, xd);
     }
     if (active) {
       split_state<PREC, DIM>(xh, xl, xd);

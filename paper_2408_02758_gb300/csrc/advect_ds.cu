@@ -247,6 +247,168 @@ __global__ void __launch_bounds__(32) k_advect_ds_dg_pair(AdvArgs a) {
   }
 }
 
+// ------------------------------------------------------- run-parallel re-advection (2D gyre)
+//
+// The compensated advection leaves each node's (hi, lo) state at the boundaries of kSegments runs
+// of seg_len steps.  Here the runs of a node are integrated side by side in float-float, each
+// from its boundary state x_j (run 0 from the exact initial point), and each also carries the
+// tangent of the RK4 map over the run, J_j = d(run end)/d(run start), in float.  The boundary
+// states are the compensated flowmap's, off the float-float trajectory by delta_j ~ 1e-8, so
+// with F_j the float-float end of run j and x_{j+1} the next boundary state,
+//   delta_0 = 0,   delta_{j+1} = J_j delta_j + (F_j - x_{j+1}),   x(T) = F_last + J_last delta_last,
+// to first order in delta; the second-order term, ~|delta|^2 |d^2 Phi|, is near 1e-15, below the
+// float-float accuracy these nodes need.  The chain of dependent steps is one run long instead
+// of the whole horizon.  RK4 applied to the variational equation J' = grad(v) J alongside the
+// state gives exactly the derivative of the RK4 map.
+
+// a(t_m) = eps sin(omega t_m) at the half steps t_m = t0 + m h/2, m = 0 .. 2 nsteps, float-float
+__global__ void k_ds_coef_table(double t0, double h, double eps, double omega, int nsteps, dsf* tab) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m <= 2 * nsteps) tab[m] = ds_from_double(eps * sin(omega * (t0 + 0.5 * h * (double)m)));
+}
+
+// ds_pair_dg_vel plus this lane's row of the velocity gradient in float (piA = pi A):
+//   lane 0, u = -pi A sin(pi f) cos(pi y):  du/dx = -pi^2 A f_x cos(pi f) cos(pi y),
+//                                          du/dy =  pi^2 A sin(pi f) sin(pi y);
+//   lane 1, v = pi A cos(pi f) sin(pi y) f_x:  dv/dx = pi A sin(pi y) (2 a cos(pi f) - pi f_x^2 sin(pi f)),
+//                                              dv/dy = pi^2 A cos(pi f) cos(pi y) f_x.
+__device__ __forceinline__ dsf ds_pair_dg_vel_tan(const DsPairConst& K, const dsf& y, const dsf& ca, const dsf& hc,
+                                                  float piA, float& gx, float& gy) {
+  const float kPiF = 3.14159265358979323846f;
+  const dsf ap = K.p ? ds_make(0.f, 0.f) : ca;
+  const dsf bp = K.p ? ds_make(1.0f, 0.0f) : ds_add_f(ds_make(-2.0f * ca.h, -2.0f * ca.l), 1.0f);
+  const dsf t1 = ds_mul_u(ap, y);
+  const dsf f = ds_mul(ds_add_u(t1, bp), y);
+  const dsf fx = ds_add(ds_make(2.0f * t1.h, 2.0f * t1.l), bp);
+  const dsf fq = ds_make(__shfl_xor_sync(K.mask, fx.h, 1), __shfl_xor_sync(K.mask, fx.l, 1));
+  const dsf g = ds_make(K.p ? fq.h : 1.0f, K.p ? fq.l : 0.0f);
+  const dsf scale = ds_mul(ds_mul(K.piA, g), hc);
+  dsf sn, cs;
+  ds_sincospi(f, sn, cs);
+  const dsf cq = ds_make(__shfl_xor_sync(K.mask, cs.h, 1), __shfl_xor_sync(K.mask, cs.l, 1));
+  const float sq = __shfl_xor_sync(K.mask, sn.h, 1);
+  const float S = sn.h, C = cs.h, Cq = cq.h, fo = fx.h, fp = fq.h;
+  const float gx0 = -kPiF * piA * fo * C * Cq, gy0 = kPiF * piA * S * sq;
+  const float gx1 = piA * S * fmaf(2.0f * ca.h, Cq, -kPiF * fp * fp * sq), gy1 = kPiF * piA * Cq * C * fp;
+  gx = K.p ? gx1 : gx0;
+  gy = K.p ? gy1 : gy0;
+  return ds_mul_u(ds_mul_u(sn, cq), scale);
+}
+
+// This lane's tangent row times the stage gradient: (g . J)_p with J's rows on lanes 0 and 1.
+__device__ __forceinline__ float2 ds_pair_tan_row(const DsPairConst& K, float gx, float gy, float2 jr) {
+  const float2 jq = make_float2(__shfl_xor_sync(K.mask, jr.x, 1), __shfl_xor_sync(K.mask, jr.y, 1));
+  const float2 r0 = K.p ? jq : jr, r1 = K.p ? jr : jq;
+  return make_float2(fmaf(gx, r0.x, gy * r1.x), fmaf(gx, r0.y, gy * r1.y));
+}
+
+// ds_pair_dg_step with the tangent row jr (row p of J) advanced by the same RK4 step.
+__device__ __forceinline__ dsf ds_pair_dg_step_tan(const DsPairConst& K, const dsf& x, float2& jr, const dsf& c0,
+                                                   const dsf& c1, const dsf& c2, float piA, float h) {
+  float gx, gy;
+  const dsf d1 = ds_pair_dg_vel_tan(K, x, c0, K.h2, piA, gx, gy);
+  const float2 k1 = ds_pair_tan_row(K, gx, gy, jr);
+  const dsf d2 = ds_pair_dg_vel_tan(K, ds_add_u(x, d1), c1, K.h2, piA, gx, gy);
+  const float2 k2 = ds_pair_tan_row(K, gx, gy, make_float2(fmaf(0.5f * h, k1.x, jr.x), fmaf(0.5f * h, k1.y, jr.y)));
+  const dsf d3 = ds_pair_dg_vel_tan(K, ds_add_u(x, d2), c1, K.h, piA, gx, gy);
+  const float2 k3 = ds_pair_tan_row(K, gx, gy, make_float2(fmaf(0.5f * h, k2.x, jr.x), fmaf(0.5f * h, k2.y, jr.y)));
+  const dsf e4 = ds_pair_dg_vel_tan(K, ds_add_u(x, d3), c2, K.h6, piA, gx, gy);
+  const float2 k4 = ds_pair_tan_row(K, gx, gy, make_float2(fmaf(h, k3.x, jr.x), fmaf(h, k3.y, jr.y)));
+  const float h6 = h * (1.0f / 6.0f);
+  jr.x = fmaf(h6, fmaf(2.0f, k2.x + k3.x, k1.x + k4.x), jr.x);
+  jr.y = fmaf(h6, fmaf(2.0f, k2.y + k3.y, k1.y + k4.y), jr.y);
+  const dsf sum = ds_add(ds_add(d1, d3), ds_make(2.0f * d2.h, 2.0f * d2.l));
+  return ds_add(x, ds_add(ds_mul(sum, K.third), e4));
+}
+
+// Persistent blocks of 128 threads; a warp takes two nodes, each on 16 lanes: run j on lanes
+// 2j (x) and 2j + 1 (y).  `tab` holds the coefficient table (k_ds_coef_table).
+template <typename CT>
+__global__ void __launch_bounds__(128) k_refine_runs_dg(AdvArgs a, const dsf* __restrict__ coef) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dsf* tab = reinterpret_cast<dsf*>(smem_raw);
+  for (int m = threadIdx.x; m <= 2 * a.nsteps; m += blockDim.x) tab[m] = coef[m];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int run = (lane >> 1) & (kSegments - 1);
+  const int grp = lane & 16;  // first lane of this node's group
+  const DsPairConst K = ds_pair_const(a, true);
+  const float piA = (float)(kPi * a.p[0]);
+  const float h = (float)a.h;
+  const int L = a.seg_len;
+  const int64_t count = (int64_t)*a.list_count;
+  const int per_block = blockDim.x / 16;
+  for (int64_t base = (int64_t)blockIdx.x * per_block; base < count; base += (int64_t)gridDim.x * per_block) {
+    const int64_t slot = base + (threadIdx.x >> 4);
+    const bool active = slot < count;
+    const int64_t i = active ? (int64_t)a.list[slot] : 0;
+    const float xc = active ? (float)__ldg(reinterpret_cast<const CT*>(a.coords) + K.p * a.n_mesh + i) : 0.f;
+    dsf x;
+    if (run == 0) {
+      x = ds_from_double(active ? (double)__ldg(reinterpret_cast<const CT*>(a.coords) + K.p * a.n_mesh + i) : 0.0);
+    } else {
+      const float2 c = active ? a.seg[(int64_t)(run - 1) * a.seg_stride + K.p * a.n_mesh + i] : make_float2(0.f, 0.f);
+      x = ds_make(c.x, c.y);
+    }
+    float2 jr = make_float2(K.p == 0 ? 1.0f : 0.0f, K.p == 0 ? 0.0f : 1.0f);
+    const int k0 = run * L;
+    for (int s = 0; s < L; ++s) {  // the same count on every lane; steps past nsteps are discarded
+      const int k = k0 + s;
+      const bool live = k < a.nsteps;
+      const int m = live ? 2 * k : 0;
+      float2 jn = jr;
+      const dsf xn = ds_pair_dg_step_tan(K, x, jn, tab[m], tab[m + 1], tab[m + 2], piA, h);
+      if (live) {
+        x = xn;
+        jr = jn;
+      }
+    }
+    // r_j = F_j - x_{j+1} (float), then delta along the runs, broadcast from each run's lanes
+    float r = 0.f;
+    if (run < kSegments - 1) {
+      const float2 c = active ? a.seg[(int64_t)run * a.seg_stride + K.p * a.n_mesh + i] : make_float2(0.f, 0.f);
+      const dsf dr = ds_add(x, ds_neg(ds_make(c.x, c.y)));
+      r = dr.h + dr.l;
+    }
+    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < kSegments - 1; ++j) {
+      const int l0 = grp + 2 * j, l1 = l0 + 1;
+      const float a00 = __shfl_sync(0xffffffffu, jr.x, l0), a01 = __shfl_sync(0xffffffffu, jr.y, l0);
+      const float a10 = __shfl_sync(0xffffffffu, jr.x, l1), a11 = __shfl_sync(0xffffffffu, jr.y, l1);
+      const float r0 = __shfl_sync(0xffffffffu, r, l0), r1 = __shfl_sync(0xffffffffu, r, l1);
+      const float n0 = fmaf(a00, d0, fmaf(a01, d1, r0));
+      const float n1 = fmaf(a10, d0, fmaf(a11, d1, r1));
+      d0 = n0;
+      d1 = n1;
+    }
+    x = ds_add_f(x, fmaf(jr.x, d0, jr.y * d1));  // meaningful on the last run's lanes
+    const float qc = __shfl_xor_sync(0xffffffffu, xc, 1);
+    const float qh = __shfl_xor_sync(0xffffffffu, x.h, 1), ql = __shfl_xor_sync(0xffffffffu, x.l, 1);
+    if (active && run == kSegments - 1) {
+      reinterpret_cast<float2*>(a.out)[K.p * a.n_mesh + i] = make_float2(x.h, x.l);
+      if (a.rec && K.p == 0) {
+        const float xs[2] = {xc, qc}, ph[2] = {x.h, qh}, pl[2] = {x.l, ql};
+        store_record<2>(a.rec, i, xs, ph, pl);
+      }
+    }
+  }
+}
+
+int launch_refine_runs_dg(bool coord64, const AdvArgs& args, void* coef_ws, int grid, cudaStream_t s) {
+  dsf* coef = reinterpret_cast<dsf*>(coef_ws);
+  const int entries = 2 * args.nsteps + 1;
+  k_ds_coef_table<<<(entries + 255) / 256, 256, 0, s>>>(args.t0, args.h, args.p[1], args.p[2], args.nsteps, coef);
+  FTLE_LAUNCH_CHECK("k_ds_coef_table launch");
+  const size_t smem = sizeof(dsf) * (size_t)entries;
+  if (coord64)
+    k_refine_runs_dg<double><<<grid, 128, smem, s>>>(args, coef);
+  else
+    k_refine_runs_dg<float><<<grid, 128, smem, s>>>(args, coef);
+  FTLE_LAUNCH_CHECK("k_refine_runs_dg launch");
+  return FTLE_OK;
+}
+
 // Batched double-gyre re-advection on lane pairs: the list holds (instance, node) pairs, one per
 // lane pair, so pairs of one warp may belong to instances with different steps and parameters
 // (the shuffles name only the pair's two lanes).  Each pair forms its own coefficients

@@ -65,6 +65,8 @@ WsLayout ws_layout(int64_t n) {
   off += align256(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
   L.bitmap = off;
   off += align256(sizeof(uint32_t) * (size_t)((n + 31) / 32 + 1));
+  L.coef = off;
+  off += align256(sizeof(float) * 2 * (size_t)(2 * kSegMaxSteps + 1));
   L.total = off;
   return L;
 }
@@ -283,7 +285,15 @@ int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
   a.list_count = &hdr->n_readvected;
   a.lanes = L.refine_lanes;
   a.rec = rec_ptr(m, phi, precision);
-  rc = launch_advect_ds(fl->kind, m->dim, m->coord_fp64 != 0, a, sms * 8, 32, s);
+  if (fl->kind == FTLE_FLOW_DOUBLE_GYRE && m->dim == 2 && nsteps <= kSegMaxSteps && nsteps >= kSegments) {
+    // the flowmap carries its run boundary states (ftle_advect writes them for compensated 2D)
+    a.seg = reinterpret_cast<float2*>(reinterpret_cast<char*>(phi) + seg_offset(2, m->n_nodes));
+    a.seg_stride = (int64_t)(seg_slot_bytes(m->n_nodes) / sizeof(float2));
+    a.seg_len = seg_len(nsteps);
+    rc = launch_refine_runs_dg(m->coord_fp64 != 0, a, w + W.coef, sms * 8, s);
+  } else {
+    rc = launch_advect_ds(fl->kind, m->dim, m->coord_fp64 != 0, a, sms * 8, 32, s);
+  }
   if (rc) return rc;
   return launch_grad_f64(m->dim, PHI32PAIR, m->coord_fp64 != 0, false, g, sms * 4, 128, s);
 }
@@ -297,6 +307,11 @@ int run_advect(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
   a.ckpt_every = ckpt ? ckpt_every : 0;
   a.ckpt_stride_bytes = (int64_t)ftle_checkpoint_bytes(m->dim, m->n_nodes, precision);
   a.rec = rec_ptr(m, phi, precision);
+  if (precision == FTLE_PREC_FP32C && m->dim == 2) {
+    a.seg = reinterpret_cast<float2*>(reinterpret_cast<char*>(phi) + seg_offset(2, m->n_nodes));
+    a.seg_stride = (int64_t)(seg_slot_bytes(m->n_nodes) / sizeof(float2));
+    a.seg_len = seg_len(nsteps);
+  }
   const int prec = precision == FTLE_PREC_FP64 ? P64 : (precision == FTLE_PREC_FP32 ? P32 : P32C);
   const int out = precision == FTLE_PREC_FP64 ? O64 : (precision == FTLE_PREC_FP32 ? O32 : O32PAIR);
   int block = L.advect_block;
@@ -341,6 +356,8 @@ size_t ftle_checkpoint_bytes(int32_t dim, int64_t n_nodes, int32_t precision) {
 
 size_t ftle_flowmap_bytes(int32_t dim, int64_t n_nodes, int32_t precision) {
   if ((dim != 2 && dim != 3) || n_nodes < 0) return 0;
+  if (precision == FTLE_PREC_FP32C && dim == 2)
+    return seg_offset(dim, n_nodes) + (size_t)(kSegments - 1) * seg_slot_bytes(n_nodes);
   if (precision == FTLE_PREC_FP32C) return rec_offset(dim, n_nodes) + 32 * (size_t)n_nodes;
   return ftle_checkpoint_bytes(dim, n_nodes, precision);
 }

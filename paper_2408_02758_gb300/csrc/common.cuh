@@ -36,8 +36,13 @@ struct WsLayout {
   size_t flag_list = 0;  // int32 [n]
   size_t mark_list = 0;  // int32 [n]
   size_t bitmap = 0;     // uint32 [ceil(n/32)]
+  size_t coef = 0;       // float-float a(t) at the half steps of a run-parallel re-advection
   size_t total = 0;
 };
+
+// Longest step count the run-parallel re-advection takes (its coefficient table of 2 n + 1
+// float-float values lives in the workspace and in each block's shared memory).
+constexpr int kSegMaxSteps = 2047;
 WsLayout ws_layout(int64_t n);
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -118,6 +123,19 @@ __device__ __forceinline__ void fsincos(float x, float& s, float& c) { fsincos_c
 // position.  The full (hi, lo) pairs stay in the flowmap for the FP64 paths.
 __host__ __device__ inline size_t rec_offset(int dim, int64_t n) {
   return ((size_t)8 * (size_t)dim * (size_t)n + 255) & ~size_t(255);
+}
+
+// A compensated 2D flowmap carries, after its records, the (hi, lo) state of every node at the
+// kSegments - 1 interior boundaries of kSegments equal runs of steps (run length
+// seg_len(nsteps), the last run shorter): the starting points from which the float-float
+// re-advection integrates the runs side by side.  Slot j (j = 0 .. kSegments - 2) holds the state
+// after min((j + 1) seg_len, nsteps) steps, laid out like the (hi, lo) pairs, float2 [2][n].
+constexpr int kSegments = 8;
+
+__host__ __device__ inline int seg_len(int nsteps) { return (nsteps + kSegments - 1) / kSegments; }
+__host__ __device__ inline size_t seg_slot_bytes(int64_t n) { return ((size_t)16 * (size_t)n + 255) & ~size_t(255); }
+__host__ __device__ inline size_t seg_offset(int dim, int64_t n) {
+  return rec_offset(dim, n) + (((size_t)32 * (size_t)n + 255) & ~size_t(255));
 }
 
 __device__ __forceinline__ uint32_t bf16_bits(float v) {  // round to nearest even

@@ -69,6 +69,8 @@ def test_status_strings_and_host_side_validation():
     rc = L.ftle_advect(ctypes.byref(m), ctypes.byref(f), 0.0, 1e12, 1e-3, 2, None, None, 0, None, None)
     assert rc == ftle.FTLE_ERANGE
     # fp32c: (hi, lo) pairs, then 32-byte gradient records at the next 256-byte boundary
-    assert L.ftle_flowmap_bytes(2, 10, 2) == 256 + 32 * 10 and L.ftle_flowmap_bytes(3, 10, 1) == 120
+    # 2D fp32c: then 7 run-boundary states (float2 [2][n] each, 256-byte aligned)
+    assert L.ftle_flowmap_bytes(2, 10, 2) == 256 + 512 + 7 * 256 and L.ftle_flowmap_bytes(3, 10, 1) == 120
+    assert L.ftle_flowmap_bytes(3, 10, 2) == 256 + 32 * 10
     assert L.ftle_checkpoint_bytes(2, 10, 2) == 160 and L.ftle_checkpoint_bytes(3, 10, 0) == 240
     assert L.ftle_workspace_bytes(1000) >= 8000

@@ -289,6 +289,28 @@ def test_float_float_readvection_matches_fp64_flowmap(F):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("T", [1.23, 0.09, -4.0, 25.0])
+def test_run_parallel_readvection_matches_fp64_flowmap(F, T):
+    """The re-advected nodes' flowmap agrees with the FP64 oracle at float-float accuracy for step
+    counts that do not divide into the runs evenly (123), runs of one or two steps (9), a backward
+    horizon, and a horizon past the run-parallel table (2500 steps: the sequential kernel)."""
+    w = I.preset(1, scale=1 / 32)
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    opt = F.make_options(refine_kappa=0.05)  # a wide re-advection list
+    out = F.compute(dm, w.flow, T, w.dt, "fp32c", return_all=True, options=opt)
+    cnt = F.ftle_read_counters(out["workspace"])
+    n = w.mesh.n_nodes
+    assert cnt["n_readvected"] > 0
+    off = 256 + ((4 * n + 255) // 256) * 256
+    ws = out["workspace"].cpu().numpy()
+    marked = np.frombuffer(ws[off: off + 4 * cnt["n_readvected"]].tobytes(), dtype=np.int32)
+    ph = F.flowmap_pairs(out["phi"], 2, n).double().cpu().numpy()
+    ph = ph[..., 0] + ph[..., 1]
+    ref = O.advect(w.flow.kind, w.flow.params, w.mesh.coords[:, marked], T, w.dt)
+    err = np.abs(ph[:, marked] - ref).max()
+    assert err < 1e-10, err
+
+
 @pytest.mark.parametrize("preset,scale,kappa", [(1, 1 / 16, 0.01), (2, 1 / 8, 0.3)])
 def test_readvection_independent_of_lanes_per_block(F, preset, scale, kappa):
     """How many nodes a block of the float-float re-advection takes (refine_lanes; the 2D double
