@@ -321,25 +321,27 @@ __device__ __forceinline__ dsf ds_pair_dg_step_tan(const DsPairConst& K, const d
   return ds_add(x, ds_add(ds_mul(sum, K.third), e4));
 }
 
-// Persistent blocks of 128 threads; a warp takes two nodes, each on 16 lanes: run j on lanes
-// 2j (x) and 2j + 1 (y).  `tab` holds the coefficient table (k_ds_coef_table).
+// Persistent blocks of 128 threads; a node takes 2 kSegments lanes of one warp: run j on lanes
+// 2j (x) and 2j + 1 (y).  `coef` holds the coefficient table (k_ds_coef_table).
 template <typename CT>
 __global__ void __launch_bounds__(128) k_refine_runs_dg(AdvArgs a, const dsf* __restrict__ coef) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dsf* tab = reinterpret_cast<dsf*>(smem_raw);
   for (int m = threadIdx.x; m <= 2 * a.nsteps; m += blockDim.x) tab[m] = coef[m];
   __syncthreads();
+  constexpr int kLanes = 2 * kSegments;  // lanes per node
+  static_assert(32 % kLanes == 0, "a node's runs fit in one warp");
   const int lane = threadIdx.x & 31;
   const int run = (lane >> 1) & (kSegments - 1);
-  const int grp = lane & 16;  // first lane of this node's group
+  const int grp = lane & (32 - kLanes);  // first lane of this node's group
   const DsPairConst K = ds_pair_const(a, true);
   const float piA = (float)(kPi * a.p[0]);
   const float h = (float)a.h;
   const int L = a.seg_len;
   const int64_t count = (int64_t)*a.list_count;
-  const int per_block = blockDim.x / 16;
+  const int per_block = blockDim.x / kLanes;
   for (int64_t base = (int64_t)blockIdx.x * per_block; base < count; base += (int64_t)gridDim.x * per_block) {
-    const int64_t slot = base + (threadIdx.x >> 4);
+    const int64_t slot = base + (threadIdx.x / kLanes);
     const bool active = slot < count;
     const int64_t i = active ? (int64_t)a.list[slot] : 0;
     const float xc = active ? (float)__ldg(reinterpret_cast<const CT*>(a.coords) + K.p * a.n_mesh + i) : 0.f;
