@@ -142,17 +142,24 @@ __device__ __forceinline__ void ds_rotate(const float4 t, dsf su, dsf cu, dsf& s
   c = ds_add_u(ds_mul_u(ca, cu), ds_neg(ds_mul_u(sa, su)));
 }
 
-// sin(pi x), cos(pi x) of a float-float x: x = k/2 + r (|r| <= 1/4), r = j/64 + u (|u| <= 1/128),
-// both subtractions exact; (sin, cos)(pi j/64) from the table, pi u by the tiny series.
+// sin(pi x), cos(pi x) of a float-float x: x = 2k + r (|r| <= 1), r = j/512 + u (|u| <= 1/1024),
+// both subtractions exact; (sin, cos)(pi j/512) from a one-period table, and of t = pi u by
+//   sin t = t + t^3 (-1/6 + t^2/120),   cos t = 1 - t^2/2 + t^4/24   (Taylor).
+// With |t| <= pi/1024 the cubic part (< 5e-9) and t^4/24 (< 4e-12) are formed in float, whose
+// rounding stays below 3e-16, and the dropped terms are below 2e-15 t and 1e-18.
 __device__ __forceinline__ void ds_sincospi(dsf x, dsf& s, dsf& c) {
-  const float k = rintf(2.0f * x.h);
-  const dsf r = ds_fast(x.h - 0.5f * k, x.l);
-  const float j = rintf(64.0f * r.h);
-  const dsf u = ds_fast(r.h - j * (1.0f / 64.0f), r.l);
-  dsf su, cu, sr, cr;
-  ds_sincos_tiny(ds_mul_u(u, tc<1, true>()), su, cu);
-  ds_rotate(__ldg(reinterpret_cast<const float4*>(kDS_SINPI_TAB) + (int)j + 16), su, cu, sr, cr);
-  ds_quadrant((int)k, sr, cr, s, c);
+  const float k2 = 2.0f * rintf(0.5f * x.h);
+  const dsf r = ds_fast(x.h - k2, x.l);
+  const float j = rintf(512.0f * r.h);
+  const dsf u = ds_fast(r.h - j * (1.0f / 512.0f), r.l);
+  const dsf t = ds_mul_u(u, tc<1, true>());
+  const float t2 = t.h * t.h;
+  const dsf su = ds_fast(t.h, fmaf(t.h * t2, fmaf(t2, 1.0f / 120.0f, -1.0f / 6.0f), t.l));
+  const dsf tt = ds_mul_u(t, t);
+  const float cl = fmaf(-0.5f, tt.l, tt.h * tt.h * (1.0f / 24.0f));
+  const dsf ch = ds_fast(1.0f, -0.5f * tt.h);
+  const dsf cu = ds_make(ch.h, ch.l + cl);
+  ds_rotate(__ldg(reinterpret_cast<const float4*>(kDS_SINPI512_TAB) + (int)j + 512), su, cu, s, c);
 }
 
 // sin(x), cos(x) of a float-float x: x = k pi/2 + r (the product in float-float), r = j/32 + u

@@ -114,14 +114,6 @@ def main():
         return float(h), float(np.float32(v - float(h)))
 
     rows = []
-    for j in range(-16, 17):
-        a = math.pi * j / 64
-        sh, sl = pair(math.sin(a))
-        ch, cl = pair(math.cos(a))
-        rows.append(f"  {{{sh:.9e}f, {sl:.9e}f, {ch:.9e}f, {cl:.9e}f}}")
-    out.append("// float-float (sin, cos)(pi j / 64), j = -16..16: {sin_h, sin_l, cos_h, cos_l}")
-    out.append("__device__ __align__(16) const float kDS_SINPI_TAB[33][4] = {\n" + ",\n".join(rows) + "};")
-    rows = []
     for j in range(-26, 27):
         a = j / 32
         sh, sl = pair(math.sin(a))
@@ -129,6 +121,22 @@ def main():
         rows.append(f"  {{{sh:.9e}f, {sl:.9e}f, {ch:.9e}f, {cl:.9e}f}}")
     out.append("// float-float (sin, cos)(j / 32), j = -26..26: {sin_h, sin_l, cos_h, cos_l}")
     out.append("__device__ __align__(16) const float kDS_SIN_TAB[53][4] = {\n" + ",\n".join(rows) + "};")
+    # one period of sin/cos(pi x) at spacing 1/512, from 50-digit values rounded to float-float
+    import mpmath
+
+    mpmath.mp.dps = 50
+
+    def pair_mp(v):
+        h = np.float32(float(v))
+        return float(h), float(np.float32(float(v - mpmath.mpf(float(h)))))
+
+    rows = []
+    for j in range(-512, 513):
+        sh, sl = pair_mp(mpmath.sinpi(mpmath.mpf(j) / 512))
+        ch, cl = pair_mp(mpmath.cospi(mpmath.mpf(j) / 512))
+        rows.append(f"  {{{sh:.9e}f, {sl:.9e}f, {ch:.9e}f, {cl:.9e}f}}")
+    out.append("// float-float (sin, cos)(pi j / 512), j = -512..512: {sin_h, sin_l, cos_h, cos_l}")
+    out.append("__device__ __align__(16) const float kDS_SINPI512_TAB[1025][4] = {\n" + ",\n".join(rows) + "};")
     text = ("// Generated by gen_poly.py (Remez exchange, float32 coefficients); do not edit by hand.\n"
             "// " + "\n// ".join(report) + "\n#pragma once\n\nnamespace ftle {\n" + "\n".join(out) + "\n}  // namespace ftle\n")
     (HERE / "poly_coef.cuh").write_text(text)
