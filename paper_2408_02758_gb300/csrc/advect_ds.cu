@@ -321,6 +321,42 @@ __device__ __forceinline__ dsf ds_pair_dg_step_tan(const DsPairConst& K, const d
   return ds_add(x, ds_add(ds_mul(sum, K.third), e4));
 }
 
+// The join of a node's runs (lanes grp .. grp + 2 kSegments - 1, K.mask covering them): with x the
+// end of this lane's run (component p) and jr its tangent row, r_j = F_j - x_{j+1} (float), then
+// delta_{j+1} = J_j delta_j + r_j broadcast from each run's lanes, and the last run's end
+// corrected by J_last delta_last; the last run's lanes store the node's state and record.
+__device__ __forceinline__ void ds_runs_join_store(const AdvArgs& a, const DsPairConst& K, int grp, int run,
+                                                   bool active, int64_t i, float xc, dsf x, float2 jr) {
+  float r = 0.f;
+  if (run < kSegments - 1) {
+    const float2 c = active ? a.seg[(int64_t)run * a.seg_stride + K.p * a.n_mesh + i] : make_float2(0.f, 0.f);
+    const dsf dr = ds_add(x, ds_neg(ds_make(c.x, c.y)));
+    r = dr.h + dr.l;
+  }
+  float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < kSegments - 1; ++j) {
+    const int l0 = grp + 2 * j, l1 = l0 + 1;
+    const float a00 = __shfl_sync(K.mask, jr.x, l0), a01 = __shfl_sync(K.mask, jr.y, l0);
+    const float a10 = __shfl_sync(K.mask, jr.x, l1), a11 = __shfl_sync(K.mask, jr.y, l1);
+    const float r0 = __shfl_sync(K.mask, r, l0), r1 = __shfl_sync(K.mask, r, l1);
+    const float n0 = fmaf(a00, d0, fmaf(a01, d1, r0));
+    const float n1 = fmaf(a10, d0, fmaf(a11, d1, r1));
+    d0 = n0;
+    d1 = n1;
+  }
+  x = ds_add_f(x, fmaf(jr.x, d0, jr.y * d1));  // meaningful on the last run's lanes
+  const float qc = __shfl_xor_sync(K.mask, xc, 1);
+  const float qh = __shfl_xor_sync(K.mask, x.h, 1), ql = __shfl_xor_sync(K.mask, x.l, 1);
+  if (active && run == kSegments - 1) {
+    reinterpret_cast<float2*>(a.out)[K.p * a.n_mesh + i] = make_float2(x.h, x.l);
+    if (a.rec && K.p == 0) {
+      const float xs[2] = {xc, qc}, ph[2] = {x.h, qh}, pl[2] = {x.l, ql};
+      store_record<2>(a.rec, i, xs, ph, pl);
+    }
+  }
+}
+
 // Persistent blocks of 128 threads; a node takes 2 kSegments lanes of one warp: run j on lanes
 // 2j (x) and 2j + 1 (y).  `coef` holds the coefficient table (k_ds_coef_table).
 template <typename CT>
@@ -365,35 +401,7 @@ __global__ void __launch_bounds__(128) k_refine_runs_dg(AdvArgs a, const dsf* __
         jr = jn;
       }
     }
-    // r_j = F_j - x_{j+1} (float), then delta along the runs, broadcast from each run's lanes
-    float r = 0.f;
-    if (run < kSegments - 1) {
-      const float2 c = active ? a.seg[(int64_t)run * a.seg_stride + K.p * a.n_mesh + i] : make_float2(0.f, 0.f);
-      const dsf dr = ds_add(x, ds_neg(ds_make(c.x, c.y)));
-      r = dr.h + dr.l;
-    }
-    float d0 = 0.f, d1 = 0.f;
-#pragma unroll
-    for (int j = 0; j < kSegments - 1; ++j) {
-      const int l0 = grp + 2 * j, l1 = l0 + 1;
-      const float a00 = __shfl_sync(0xffffffffu, jr.x, l0), a01 = __shfl_sync(0xffffffffu, jr.y, l0);
-      const float a10 = __shfl_sync(0xffffffffu, jr.x, l1), a11 = __shfl_sync(0xffffffffu, jr.y, l1);
-      const float r0 = __shfl_sync(0xffffffffu, r, l0), r1 = __shfl_sync(0xffffffffu, r, l1);
-      const float n0 = fmaf(a00, d0, fmaf(a01, d1, r0));
-      const float n1 = fmaf(a10, d0, fmaf(a11, d1, r1));
-      d0 = n0;
-      d1 = n1;
-    }
-    x = ds_add_f(x, fmaf(jr.x, d0, jr.y * d1));  // meaningful on the last run's lanes
-    const float qc = __shfl_xor_sync(0xffffffffu, xc, 1);
-    const float qh = __shfl_xor_sync(0xffffffffu, x.h, 1), ql = __shfl_xor_sync(0xffffffffu, x.l, 1);
-    if (active && run == kSegments - 1) {
-      reinterpret_cast<float2*>(a.out)[K.p * a.n_mesh + i] = make_float2(x.h, x.l);
-      if (a.rec && K.p == 0) {
-        const float xs[2] = {xc, qc}, ph[2] = {x.h, qh}, pl[2] = {x.l, ql};
-        store_record<2>(a.rec, i, xs, ph, pl);
-      }
-    }
+    ds_runs_join_store(a, K, grp, run, active, i, xc, x, jr);
   }
 }
 
@@ -516,6 +524,71 @@ __global__ void __launch_bounds__(32) k_batch_advect_ds(const BatchInst* __restr
     }
     if (a.rec) store_record<DIM>(a.rec, i, x0, ph, pl);
   }
+}
+
+// Batched run-parallel re-advection (2D double gyre, compensated flowmaps with run-boundary
+// states): a half-warp per (instance, node) pair, run j on its lanes 2j and 2j + 1.  The two
+// halves of a warp may belong to instances with different steps, so every shuffle names only its
+// half.  Each run forms its time coefficients a(t) = eps sin(omega t) by turning
+// (sin, cos)(omega t) from its own first half step through omega h/2 per half step.
+__global__ void __launch_bounds__(128) k_batch_refine_runs_dg(const BatchInst* __restrict__ insts, const int2* pairs,
+                                                              const unsigned long long* count) {
+  const int lane = threadIdx.x & 31;
+  const int run = (lane >> 1) & (kSegments - 1);
+  const int grp = lane & 16;
+  const int64_t cnt = (int64_t)*count;
+  const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 4);
+  for (int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> 4) + (threadIdx.x >> 4); slot < cnt; slot += stride) {
+    const int2 pr = pairs[slot];
+    const AdvArgs& a = insts[pr.x].adv;
+    const int64_t i = pr.y;
+    DsPairConst K = ds_pair_const(a, false);
+    K.mask = 0xFFFFu << grp;
+    const float piA = (float)(kPi * a.p[0]);
+    const float h = (float)a.h;
+    const int L = a.seg_len;
+    const float xc = __ldg(reinterpret_cast<const float*>(a.coords) + K.p * a.n_mesh + i);
+    dsf x;
+    if (run == 0) {
+      x = ds_from_double((double)xc);
+    } else {
+      const float2 c = a.seg[(int64_t)(run - 1) * a.seg_stride + K.p * a.n_mesh + i];
+      x = ds_make(c.x, c.y);
+    }
+    const dsf eps = ds_from_double(a.p[1]);
+    const dsf rs = ds_from_double(sin(0.5 * a.p[2] * a.h)), rc = ds_from_double(cos(0.5 * a.p[2] * a.h));
+    const double t_start = a.t0 + a.h * (double)(run * L);
+    dsf sw = ds_from_double(sin(a.p[2] * t_start)), cw = ds_from_double(cos(a.p[2] * t_start));
+    auto advance = [&]() {
+      const dsf s2 = ds_add(ds_mul(sw, rc), ds_mul(cw, rs));
+      cw = ds_add(ds_mul(cw, rc), ds_neg(ds_mul(sw, rs)));
+      sw = s2;
+    };
+    float2 jr = make_float2(K.p == 0 ? 1.0f : 0.0f, K.p == 0 ? 0.0f : 1.0f);
+    dsf c2 = ds_mul(eps, sw);
+    for (int s = 0; s < L; ++s) {  // every lane of the half-warp runs L steps; past nsteps discarded
+      const bool live = run * L + s < a.nsteps;
+      const dsf c0 = c2;
+      advance();
+      const dsf c1 = ds_mul(eps, sw);
+      advance();
+      c2 = ds_mul(eps, sw);
+      float2 jn = jr;
+      const dsf xn = ds_pair_dg_step_tan(K, x, jn, c0, c1, c2, piA, h);
+      if (live) {
+        x = xn;
+        jr = jn;
+      }
+    }
+    ds_runs_join_store(a, K, grp, run, true, i, xc, x, jr);
+  }
+}
+
+int launch_batch_refine_runs_dg(const BatchInst* insts, const int2* pairs, const unsigned long long* count, int grid,
+                                cudaStream_t s) {
+  k_batch_refine_runs_dg<<<grid, 128, 0, s>>>(insts, pairs, count);
+  FTLE_LAUNCH_CHECK("k_batch_refine_runs_dg launch");
+  return FTLE_OK;
 }
 
 int launch_batch_advect_ds(int kind, int dim, const BatchInst* insts, const int2* pairs,

@@ -52,6 +52,9 @@ __global__ void __launch_bounds__(256) k_batch_advect(const BatchInst* __restric
       x0[d] = xh[d];
     }
     const int nchunks = (a.nsteps + kAdvChunk - 1) / kAdvChunk;
+    // run-boundary states of compensated 2D flowmaps (as k_advect stores them)
+    constexpr bool kSegs = PREC == P32C && OUT == O32PAIR && DIM == 2;
+    int seg_slot = 0, next_seg = a.seg_len;
     for (int ch = 0; ch < nchunks; ++ch) {
       const int k0 = ch * kAdvChunk;
       const int k1 = min(a.nsteps, k0 + kAdvChunk);
@@ -64,13 +67,29 @@ __global__ void __launch_bounds__(256) k_batch_advect(const BatchInst* __restric
         }
       }
       if (!active) continue;
-      for (int k = k0; k < k1; ++k) {
-        const int m = 2 * (k - k0);
-        const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
-        const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
-        const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
-        rk4_step<KIND, DIM, PREC>(a, c0, c1, c2, xh, xl, xd);
+      for (int k = k0; k < k1;) {
+        const int stop = (kSegs && a.seg) ? min(k1, next_seg) : k1;
+        for (; k < stop; ++k) {
+          const int m = 2 * (k - k0);
+          const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
+          const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
+          const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
+          rk4_step<KIND, DIM, PREC>(a, c0, c1, c2, xh, xl, xd);
+        }
+        if constexpr (kSegs) {
+          if (a.seg && k == next_seg) {
+            if (seg_slot < kSegments - 1)
+              store_state<OUT, DIM>(a.seg + (int64_t)seg_slot * a.seg_stride, a.n_mesh, i, xh, xl, xd);
+            ++seg_slot;
+            next_seg += a.seg_len;
+          }
+        }
       }
+    }
+    if constexpr (kSegs) {
+      if (a.seg && active)
+        for (; seg_slot < kSegments - 1; ++seg_slot)
+          store_state<OUT, DIM>(a.seg + (int64_t)seg_slot * a.seg_stride, a.n_mesh, i, xh, xl, xd);
     }
     if (active) {
       split_state<PREC, DIM>(xh, xl, xd);
@@ -301,6 +320,11 @@ int plan_batch(int32_t n_inst, const ftle_mesh* meshes, const ftle_flow* flows, 
     void* phi = P.ws + P.L.phi_off[q];
     bi.adv = make_adv_args(&meshes[q], &flows[q], 0.0, T[q], dt, nsteps);
     bi.adv.out = phi;
+    if (precision == FTLE_PREC_FP32C && meshes[q].dim == 2) {
+      bi.adv.seg = reinterpret_cast<float2*>(reinterpret_cast<char*>(phi) + seg_offset(2, meshes[q].n_nodes));
+      bi.adv.seg_stride = (int64_t)(seg_slot_bytes(meshes[q].n_nodes) / sizeof(float2));
+      bi.adv.seg_len = seg_len(nsteps);
+    }
     float4* rec = precision == FTLE_PREC_FP32C
                       ? reinterpret_cast<float4*>(reinterpret_cast<char*>(phi) + rec_offset(meshes[q].dim, meshes[q].n_nodes))
                       : nullptr;
@@ -366,7 +390,11 @@ int enqueue_batch(const BatchPlanHost& P, cudaStream_t s) {
   if ((rc = launch_batch_mark(insts, flags, &hdr->n_flagged, marks, &hdr->n_readvected,
                               reinterpret_cast<uint32_t*>(w + P.L.bitmap), sms * 4, 128, s)))
     return rc;
-  if ((rc = launch_batch_advect_ds(P.kind, P.dim, insts, marks, &hdr->n_readvected, sms * 8, 32, s))) return rc;
+  if (P.kind == FTLE_FLOW_DOUBLE_GYRE && P.dim == 2 && P.precision == FTLE_PREC_FP32C)
+    rc = launch_batch_refine_runs_dg(insts, marks, &hdr->n_readvected, sms * 8, s);
+  else
+    rc = launch_batch_advect_ds(P.kind, P.dim, insts, marks, &hdr->n_readvected, sms * 8, 32, s);
+  if (rc) return rc;
   return launch_batch_grad_f64(P.dim, pl, insts, flags, &hdr->n_flagged, sms * 4, 128, s);
 }
 

@@ -32,6 +32,10 @@ int launch_batch_grad_f64(int dim, int phi_layout, const BatchInst* insts, const
                           const unsigned long long* count, int grid, int block, cudaStream_t s);
 int launch_batch_mark(const BatchInst* insts, const int2* flags, const unsigned long long* n_flags, int2* marks,
                       unsigned long long* n_marks, uint32_t* bitmap, int grid, int block, cudaStream_t s);
+// Run-parallel batched re-advection of compensated 2D double-gyre instances (every instance's
+// flowmap carries its run-boundary states).
+int launch_batch_refine_runs_dg(const BatchInst* insts, const int2* pairs, const unsigned long long* count, int grid,
+                                cudaStream_t s);
 int launch_batch_advect_ds(int kind, int dim, const BatchInst* insts, const int2* pairs,
                            const unsigned long long* count, int grid, int block, cudaStream_t s);
 
