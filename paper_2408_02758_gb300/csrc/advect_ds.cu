@@ -419,45 +419,6 @@ int launch_refine_runs_dg(bool coord64, const AdvArgs& args, void* coef_ws, int 
   return FTLE_OK;
 }
 
-// Batched double-gyre re-advection on lane pairs: the list holds (instance, node) pairs, one per
-// lane pair, so pairs of one warp may belong to instances with different steps and parameters
-// (the shuffles name only the pair's two lanes).  Each pair forms its own coefficients
-// a(t_m) = eps sin(omega t_m) at the half steps t_m = t0 + m h/2 by turning (sin, cos)(omega t_m)
-// through the fixed angle omega h/2 with the angle-addition formulas in float-float: four
-// products and two sums per half step, off the state's dependency chain (rounding grows like
-// the square root of the half-step count, ~1e-13 relative after 3000 half steps).
-__global__ void __launch_bounds__(32) k_batch_advect_ds_dg_pair(const BatchInst* __restrict__ insts,
-                                                                const int2* pairs, const unsigned long long* count) {
-  const int64_t cnt = (int64_t)*count;
-  const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 1);
-  for (int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> 1) + (threadIdx.x >> 1); slot < cnt; slot += stride) {
-    const int2 pr = pairs[slot];
-    const AdvArgs& a = insts[pr.x].adv;
-    const int64_t i = pr.y;
-    const DsPairConst K = ds_pair_const(a, false);
-    const dsf eps = ds_from_double(a.p[1]);
-    const dsf rs = ds_from_double(sin(0.5 * a.p[2] * a.h)), rc = ds_from_double(cos(0.5 * a.p[2] * a.h));
-    dsf sw = ds_from_double(sin(a.p[2] * a.t0)), cw = ds_from_double(cos(a.p[2] * a.t0));
-    auto advance = [&]() {  // (sin, cos)(omega t) -> (sin, cos)(omega (t + h/2))
-      const dsf s2 = ds_add(ds_mul(sw, rc), ds_mul(cw, rs));
-      cw = ds_add(ds_mul(cw, rc), ds_neg(ds_mul(sw, rs)));
-      sw = s2;
-    };
-    dsf x = ds_from_double((double)__ldg(reinterpret_cast<const float*>(a.coords) + K.p * a.n_mesh + i));
-    const float x0 = x.h;
-    dsf c2 = ds_mul(eps, sw);
-    for (int k = 0; k < a.nsteps; ++k) {
-      const dsf c0 = c2;
-      advance();
-      const dsf c1 = ds_mul(eps, sw);
-      advance();
-      c2 = ds_mul(eps, sw);
-      x = ds_pair_dg_step(K, x, c0, c1, c2);
-    }
-    ds_pair_store(a, K, i, true, x0, x);
-  }
-}
-
 // Batched re-advection: the list holds (instance, node) pairs, so lanes of one warp may belong
 // to different instances; each lane forms its own double-gyre coefficient a(t_m) =
 // eps sin(omega t_m) in float-float (t_m = t0 + m h/2) instead of reading a shared table.
@@ -593,7 +554,7 @@ int launch_batch_refine_runs_dg(const BatchInst* insts, const int2* pairs, const
 
 int launch_batch_advect_ds(int kind, int dim, const BatchInst* insts, const int2* pairs,
                            const unsigned long long* count, int grid, int block, cudaStream_t s) {
-  if (kind == FTLE_FLOW_DOUBLE_GYRE && dim == 2) k_batch_advect_ds_dg_pair<<<2 * grid, block, 0, s>>>(insts, pairs, count);
+  if (kind == FTLE_FLOW_DOUBLE_GYRE && dim == 2) k_batch_advect_ds<FTLE_FLOW_DOUBLE_GYRE, 2><<<grid, block, 0, s>>>(insts, pairs, count);
   else if (kind == FTLE_FLOW_ABC && dim == 3) k_batch_advect_ds<FTLE_FLOW_ABC, 3><<<grid, block, 0, s>>>(insts, pairs, count);
   else if (kind == FTLE_FLOW_LINEAR && dim == 2) k_batch_advect_ds<FTLE_FLOW_LINEAR, 2><<<grid, block, 0, s>>>(insts, pairs, count);
   else if (kind == FTLE_FLOW_LINEAR && dim == 3) k_batch_advect_ds<FTLE_FLOW_LINEAR, 3><<<grid, block, 0, s>>>(insts, pairs, count);
