@@ -106,14 +106,11 @@ struct DgDer {
   float q0, q1;            // du/deps = s q, du/domega = eps t c q
 };
 
-// Double-gyre velocity and derivatives at (x, y), coefficients a = eps s, b = 1 - 2a.
-__device__ __forceinline__ DgDer dg_derivs32(float piA, float a, float b, float x, float y) {
+// Double-gyre velocity and derivatives at a point with abscissa x, from the slope f_x of the
+// stream function's argument and (sin, cos) of pi f and of pi y there; coefficient a = eps s.
+__device__ __forceinline__ DgDer dg_derivs_sc(float piA, float a, float fx, float x, float sf, float cf, float sy,
+                                              float cy) {
   const float kPiF = 3.14159265358979323846f;
-  const float f = fmaf(a, x, b) * x;
-  const float fx = fmaf(2.0f * a, x, b);
-  float sf, cf, sy, cy;
-  fsincospi(f, sf, cf);
-  fsincospi(y, sy, cy);
   DgDer d;
   d.u0 = -piA * sf * cy;
   d.u1 = piA * cf * sy * fx;
@@ -128,6 +125,31 @@ __device__ __forceinline__ DgDer dg_derivs32(float piA, float a, float b, float 
   d.q0 = -pi2A * cf * cy * g1;
   d.q1 = piA * sy * fmaf(-kPiF * sf * g1, fx, cf * g2);
   return d;
+}
+
+// ... at (x, y) with coefficients a, b = 1 - 2a, evaluating the sines and cosines.
+__device__ __forceinline__ DgDer dg_derivs32(float piA, float a, float b, float x, float y) {
+  const float f = fmaf(a, x, b) * x;
+  float sf, cf, sy, cy;
+  fsincospi(f, sf, cf);
+  fsincospi(y, sy, cy);
+  return dg_derivs_sc(piA, a, fmaf(2.0f * a, x, b), x, sf, cf, sy, cy);
+}
+
+// ... at the stage point (xk + dx, yk + dy) of a step whose first stage point is (xk, yk), with
+// (sin, cos) of pi f and pi y there turned from stage one's pairs by the small angles, as the
+// forward step does (e1 = 2 (xk - 1), dg = (a_s - a_0) xk (xk - 2)).  `mx` collects the larger
+// angle; past kRotMax the caller evaluates the stage in full.
+__device__ __forceinline__ DgDer dg_derivs32_rot(float piA, float as, float e1, float dg, float dx, float dy,
+                                                 float sf0, float cf0, float sy0, float cy0, float xs, float& mx) {
+  const float kPiF = 3.14159265358979323846f;
+  const float w = fmaf(as, e1 + dx, 1.0f);
+  const float tf = kPiF * fmaf(dx, w, dg), ty = kPiF * dy;
+  mx = fmaxf(mx, fmaxf(fabsf(tf), fabsf(ty)));
+  float sf, cf, sy, cy;
+  rotate_small(sf0, cf0, tf, sf, cf);
+  rotate_small(sy0, cy0, ty, sy, cy);
+  return dg_derivs_sc(piA, as, fmaf(as, dx, w), xs, sf, cf, sy, cy);
 }
 
 // Segment table per half step: (a, b_l) of the forward kernel, sin(omega t), t cos(omega t).
@@ -191,14 +213,26 @@ __global__ void __launch_bounds__(kAdjBlock) k_adjoint_rk4(AdvArgs a, const floa
         const int m = 2 * (k - k0);
         const float4 t0 = tab[m], t1 = tab[m + 1], t2 = tab[m + 2];
         const float b0 = fmaf(-2.f, t0.x, 1.f), b1 = fmaf(-2.f, t1.x, 1.f), b2 = fmaf(-2.f, t2.x, 1.f);
-        // stage points (float)
-        const DgDer d1 = dg_derivs32(piA, t0.x, b0, xk.x, xk.y);
+        // stage points (float); stages two to four turn stage one's sines and cosines
+        float sf0, cf0, sy0, cy0;
+        fsincospi(fmaf(t0.x, xk.x, b0) * xk.x, sf0, cf0);
+        fsincospi(xk.y, sy0, cy0);
+        const DgDer d1 = dg_derivs_sc(piA, t0.x, fmaf(2.0f * t0.x, xk.x, b0), xk.x, sf0, cf0, sy0, cy0);
+        const float e1 = fmaf(2.0f, xk.x, -2.0f), g0 = xk.x * (xk.x - 2.0f);
+        const float dg1 = (t1.x - t0.x) * g0, dg2 = (t2.x - t0.x) * g0;
+        float mx = 0.0f;
         const float y2x = fmaf(h2, d1.u0, xk.x), y2y = fmaf(h2, d1.u1, xk.y);
-        const DgDer d2 = dg_derivs32(piA, t1.x, b1, y2x, y2y);
+        DgDer d2 = dg_derivs32_rot(piA, t1.x, e1, dg1, y2x - xk.x, y2y - xk.y, sf0, cf0, sy0, cy0, y2x, mx);
         const float y3x = fmaf(h2, d2.u0, xk.x), y3y = fmaf(h2, d2.u1, xk.y);
-        const DgDer d3 = dg_derivs32(piA, t1.x, b1, y3x, y3y);
+        DgDer d3 = dg_derivs32_rot(piA, t1.x, e1, dg1, y3x - xk.x, y3y - xk.y, sf0, cf0, sy0, cy0, y3x, mx);
         const float y4x = fmaf(h, d3.u0, xk.x), y4y = fmaf(h, d3.u1, xk.y);
-        const DgDer d4 = dg_derivs32(piA, t2.x, b2, y4x, y4y);
+        DgDer d4 = dg_derivs32_rot(piA, t2.x, e1, dg2, y4x - xk.x, y4y - xk.y, sf0, cf0, sy0, cy0, y4x, mx);
+        if (!(mx <= kRotMax)) {  // a step too long for the small-angle turns
+          d2 = dg_derivs32(piA, t1.x, b1, y2x, y2y);
+          const float z3x = fmaf(h2, d2.u0, xk.x), z3y = fmaf(h2, d2.u1, xk.y);
+          d3 = dg_derivs32(piA, t1.x, b1, z3x, z3y);
+          d4 = dg_derivs32(piA, t2.x, b2, fmaf(h, d3.u0, xk.x), fmaf(h, d3.u1, xk.y));
+        }
         float kb1x = h6 * lam0, kb1y = h6 * lam1, kb2x = h3 * lam0, kb2y = h3 * lam1;
         float kb3x = h3 * lam0, kb3y = h3 * lam1;
         const float kb4x = h6 * lam0, kb4y = h6 * lam1;
