@@ -139,11 +139,19 @@ __global__ void __launch_bounds__(256) k_batch_grad(const BatchInst* __restrict_
 template <int DIM, int PL>
 __global__ void __launch_bounds__(128) k_batch_grad_f64(const BatchInst* __restrict__ insts, const int2* pairs,
                                                         const unsigned long long* count) {
-  const int64_t cnt = (int64_t)*count;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < cnt; s += (int64_t)gridDim.x * blockDim.x) {
-    const int2 p = pairs[s];
-    grad_node_f64<DIM, PL, float, float>(insts[p.x].grad, p.y);
-  }
+  grad_list_f64<DIM>(
+      (int64_t)*count, kF64Lanes<DIM>,
+      [=](int64_t slot, int sub, int L, double* m, double* b) {
+        const int2 p = pairs[slot];
+        const GradArgs& a = insts[p.x].grad;
+        const int rs = __ldg(a.row_ptr + p.y), re = __ldg(a.row_ptr + p.y + 1);
+        grad_moments_f64<DIM, PL, float>(a, p.y, rs + sub, re, L, m, b);
+        return re - rs;
+      },
+      [=](int64_t slot, int k, const double* m, const double* b) {
+        const int2 p = pairs[slot];
+        grad_finish_f64<DIM, float>(insts[p.x].grad, p.y, k, m, b);
+      });
 }
 
 __device__ __forceinline__ void batch_mark_node(int inst, int j, int64_t off, uint32_t* bitmap, int2* marks,

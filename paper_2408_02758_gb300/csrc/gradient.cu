@@ -80,13 +80,22 @@ __global__ void __launch_bounds__(256) k_grad_f32_ell(GradArgs a) {
 
 // ----------------------------------------------------------------------------- double kernel
 
+// Every node (FTLE_PREC_FP64) or the nodes of a list, with lanes per node as the list's length
+// allows (grad_list_f64).
 template <int DIM, int PL, typename CT, typename OT>
 __global__ void __launch_bounds__(128) k_grad_f64(GradArgs a) {
   const int64_t count = a.list ? (int64_t)*a.list_count : a.n;
-  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < count;
-       slot += (int64_t)gridDim.x * blockDim.x) {
-    grad_node_f64<DIM, PL, CT, OT>(a, a.list ? (int64_t)a.list[slot] : slot);
-  }
+  grad_list_f64<DIM>(
+      count, kF64Lanes<DIM>,
+      [=](int64_t slot, int sub, int L, double* m, double* b) {
+        const int64_t i = a.list ? (int64_t)a.list[slot] : slot;
+        const int rs = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+        grad_moments_f64<DIM, PL, CT>(a, i, rs + sub, re, L, m, b);
+        return re - rs;
+      },
+      [=](int64_t slot, int k, const double* m, const double* b) {
+        grad_finish_f64<DIM, OT>(a, a.list ? (int64_t)a.list[slot] : slot, k, m, b);
+      });
 }
 
 // ----------------------------------------------------------------------------- refine marks

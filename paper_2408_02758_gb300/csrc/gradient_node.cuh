@@ -312,25 +312,30 @@ __device__ __forceinline__ bool grad_node_f32_ell_any(const GradArgs& a, int64_t
   return grad_finish_f32<DIM>(a, i, k, m, b);
 }
 
-// One node in double: the least-squares fit, mu = lambda_max(F^T F - I), FTLE; counts and NaNs
-// rank-deficient neighbourhoods.
-template <int DIM, int PL, typename CT, typename OT>
-__device__ __forceinline__ void grad_node_f64(const GradArgs& a, int64_t i) {
+// Double moments M = sum dx dx^T (upper triangle), B = sum dphi dx^T of node i over the CSR
+// entries e0, e0 + step, ... < e1: the whole row (step 1) or one lane's share of it.
+template <int DIM, int PL, typename CT>
+__device__ __forceinline__ void grad_moments_f64(const GradArgs& a, int64_t i, int e0, int e1, int step, double* m,
+                                                 double* b) {
   const int64_t n = a.n;
-  const int rs = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
-  double xi[DIM], pi[DIM];
+  double xi[DIM], pi[DIM], pil[DIM];  // node i: coordinates, flowmap (hi and lo parts of a pair)
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     xi[d] = (double)ldc<CT>(a.coords, d * n + i);
-    pi[d] = 0.0;
+    if constexpr (PL == PHI32PAIR) {
+      const float2 pv = __ldg(reinterpret_cast<const float2*>(a.phi) + d * n + i);
+      pi[d] = (double)pv.x;
+      pil[d] = (double)pv.y;
+    } else {
+      pi[d] = ld_phi64<PL>(a.phi, d * n + i);
+      pil[d] = 0.0;
+    }
   }
-  constexpr int NM = DIM * (DIM + 1) / 2;
-  double m[NM], b[DIM * DIM];
 #pragma unroll
-  for (int q = 0; q < NM; ++q) m[q] = 0.0;
+  for (int q = 0; q < DIM * (DIM + 1) / 2; ++q) m[q] = 0.0;
 #pragma unroll
   for (int q = 0; q < DIM * DIM; ++q) b[q] = 0.0;
-  for (int e = rs; e < re; ++e) {
+  for (int e = e0; e < e1; e += step) {
     const int j = __ldg(a.col_idx + e);
     double dx[DIM], dp[DIM];
 #pragma unroll
@@ -338,10 +343,9 @@ __device__ __forceinline__ void grad_node_f64(const GradArgs& a, int64_t i) {
       dx[d] = (double)ldc<CT>(a.coords, d * n + j) - xi[d];
       if constexpr (PL == PHI32PAIR) {
         const float2 pj = __ldg(reinterpret_cast<const float2*>(a.phi) + d * n + j);
-        const float2 pv = __ldg(reinterpret_cast<const float2*>(a.phi) + d * n + i);
-        dp[d] = ((double)pj.x - (double)pv.x) + ((double)pj.y - (double)pv.y);
+        dp[d] = ((double)pj.x - pi[d]) + ((double)pj.y - pil[d]);
       } else {
-        dp[d] = ld_phi64<PL>(a.phi, d * n + j) - ld_phi64<PL>(a.phi, d * n + i);
+        dp[d] = ld_phi64<PL>(a.phi, d * n + j) - pi[d];
       }
     }
     int q = 0;
@@ -354,9 +358,14 @@ __device__ __forceinline__ void grad_node_f64(const GradArgs& a, int64_t i) {
 #pragma unroll
       for (int c = 0; c < DIM; ++c) b[r * DIM + c] = fma(dp[r], dx[c], b[r * DIM + c]);
   }
-  (void)pi;
+}
+
+// From the double moments of k neighbours: F = B M^-1, mu = lambda_max(F^T F - I), FTLE and
+// lambda_max to the outputs; counts and NaNs rank-deficient neighbourhoods.
+template <int DIM, typename OT>
+__device__ __forceinline__ void grad_finish_f64(const GradArgs& a, int64_t i, int k, const double* m, const double* b) {
   double mu = NAN;
-  bool degenerate = (re - rs < DIM);
+  bool degenerate = (k < DIM);
   if (!degenerate) {
     if constexpr (DIM == 2) {
       const double det = m[0] * m[2] - m[1] * m[1];
@@ -364,8 +373,9 @@ __device__ __forceinline__ void grad_node_f64(const GradArgs& a, int64_t i) {
       if (!(det > kRankTol * 0.25 * tr * tr)) {
         degenerate = true;
       } else {
-        const double F00 = (b[0] * m[2] - b[1] * m[1]) / det, F01 = (b[1] * m[0] - b[0] * m[1]) / det;
-        const double F10 = (b[2] * m[2] - b[3] * m[1]) / det, F11 = (b[3] * m[0] - b[2] * m[1]) / det;
+        const double inv = 1.0 / det;
+        const double F00 = (b[0] * m[2] - b[1] * m[1]) * inv, F01 = (b[1] * m[0] - b[0] * m[1]) * inv;
+        const double F10 = (b[2] * m[2] - b[3] * m[1]) * inv, F11 = (b[3] * m[0] - b[2] * m[1]) * inv;
         const double e00 = fma(F00, F00, fma(F10, F10, -1.0));
         const double e11 = fma(F01, F01, fma(F11, F11, -1.0));
         const double e01 = fma(F00, F01, F10 * F11);
@@ -381,13 +391,14 @@ __device__ __forceinline__ void grad_node_f64(const GradArgs& a, int64_t i) {
       if (!(det > kRankTol * tr3 * tr3 * tr3)) {
         degenerate = true;
       } else {
+        const double inv = 1.0 / det;
         double F[9];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
           const double b0 = b[r * 3 + 0], b1 = b[r * 3 + 1], b2 = b[r * 3 + 2];
-          F[r * 3 + 0] = (b0 * a00 + b1 * a01 + b2 * a02) / det;
-          F[r * 3 + 1] = (b0 * a01 + b1 * a11 + b2 * a12) / det;
-          F[r * 3 + 2] = (b0 * a02 + b1 * a12 + b2 * a22) / det;
+          F[r * 3 + 0] = (b0 * a00 + b1 * a01 + b2 * a02) * inv;
+          F[r * 3 + 1] = (b0 * a01 + b1 * a11 + b2 * a12) * inv;
+          F[r * 3 + 2] = (b0 * a02 + b1 * a12 + b2 * a22) * inv;
         }
         double e[6];
         int q = 0;
@@ -402,11 +413,74 @@ __device__ __forceinline__ void grad_node_f64(const GradArgs& a, int64_t i) {
     }
   }
   if (degenerate) atomicAdd(&a.hdr->n_degenerate, 1ULL);
-  const double ftle = degenerate ? (double)NAN : log1p(mu) * a.inv_2absT;
+  // mu carries the double precision (lambda_max - 1 without cancellation); for a float output
+  // the logarithm of the rounded mu is as good as the double one rounded, at a fraction of the
+  // cost of double log1p on GB300
+  double lg;
+  if constexpr (sizeof(OT) == sizeof(float))
+    lg = (double)log1pf((float)mu);
+  else
+    lg = log1p(mu);
+  const double ftle = degenerate ? (double)NAN : lg * a.inv_2absT;
   reinterpret_cast<OT*>(a.ftle_out)[i] = (OT)ftle;
   if (a.lam_out) a.lam_out[i] = degenerate ? (double)NAN : 1.0 + mu;
 }
 
+// One node in double over its whole CSR row.
+template <int DIM, int PL, typename CT, typename OT>
+__device__ __forceinline__ void grad_node_f64(const GradArgs& a, int64_t i) {
+  const int rs = __ldg(a.row_ptr + i), re = __ldg(a.row_ptr + i + 1);
+  double m[DIM * (DIM + 1) / 2], b[DIM * DIM];
+  grad_moments_f64<DIM, PL, CT>(a, i, rs, re, 1, m, b);
+  grad_finish_f64<DIM, OT>(a, i, re - rs, m, b);
+}
+
+// Double work over a list of nodes with L lanes per node.  GB300 runs a warp's double
+// instruction for about the same time whatever its active lanes, so the cost is the number of
+// warps that carry double work, spread over as many SMs as possible.  A long list therefore runs
+// one node per lane (L = 1); a short one (tens of flagged nodes) gives each node up to `lmax`
+// lanes (about a row's length), as many as keep the groups within an eighth of the grid's lanes,
+// to cut the latency of its row.  The lanes of a group split the node's row, a butterfly over the
+// group sums the moments, and the group's first lane finishes the node.  Warps are numbered
+// block-fastest, so consecutive warps go to different blocks (and SMs).  moments(slot, sub, L, m, b) fills one lane's share and returns
+// the neighbour count; finish(slot, k, m, b) writes the node.
+template <int DIM, class Moments, class Finish>
+__device__ __forceinline__ void grad_list_f64(int64_t count, int lmax, Moments moments, Finish finish) {
+  constexpr int NM = DIM * (DIM + 1) / 2;
+  const int64_t threads = (int64_t)gridDim.x * blockDim.x;
+  int L = lmax;
+  while (L > 1 && count * L * 8 > threads) L >>= 1;
+  const int groups_per_warp = 32 / L;
+  const int64_t warp = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const int64_t nwarps = threads >> 5;
+  const int lane = threadIdx.x & 31, sub = lane & (L - 1);
+  for (int64_t w0 = warp * groups_per_warp; w0 < count; w0 += nwarps * groups_per_warp) {
+    const int64_t slot = w0 + lane / L;
+    const bool active = slot < count;
+    double m[NM], b[DIM * DIM];
+    int k = 0;
+    if (active) {
+      k = moments(slot, sub, L, m, b);
+    } else {
+#pragma unroll
+      for (int q = 0; q < NM; ++q) m[q] = 0.0;
+#pragma unroll
+      for (int q = 0; q < DIM * DIM; ++q) b[q] = 0.0;
+    }
+    for (int off = L >> 1; off > 0; off >>= 1) {
+#pragma unroll
+      for (int q = 0; q < NM; ++q) m[q] += __shfl_xor_sync(0xffffffffu, m[q], off);
+#pragma unroll
+      for (int q = 0; q < DIM * DIM; ++q) b[q] += __shfl_xor_sync(0xffffffffu, b[q], off);
+    }
+    if (active && sub == 0) finish(slot, k, m, b);
+  }
+}
+
+// Largest lanes per node of the double list kernels (a 2D triangle row has ~6 entries, a 3D
+// tetrahedral row ~14).
+template <int DIM>
+constexpr int kF64Lanes = DIM == 2 ? 8 : 16;
 
 __device__ __forceinline__ void mark_node(int32_t j, uint32_t* bitmap, int32_t* mark_list,
                                           unsigned long long* counter) {
