@@ -432,6 +432,30 @@ int ftle_compute(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double
   return run_refine(mesh, flow, t0, T, dt, nsteps, precision, flowmap, ftle_out, lambda_out, workspace, L, s);
 }
 
+// A second stream for copies that overlap work on the caller's stream: open() makes it wait for
+// what the caller's stream already holds, join() makes the caller's stream wait for it.
+struct SideStream {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  int open(cudaStream_t main) {
+    FTLE_CUDA_CHECK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    FTLE_CUDA_CHECK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    FTLE_CUDA_CHECK(cudaEventRecord(ev, main));
+    FTLE_CUDA_CHECK(cudaStreamWaitEvent(stream, ev, 0));
+    return FTLE_OK;
+  }
+  int join(cudaStream_t main) {
+    FTLE_CUDA_CHECK(cudaEventRecord(ev, stream));
+    FTLE_CUDA_CHECK(cudaStreamWaitEvent(main, ev, 0));
+    return FTLE_OK;
+  }
+  ~SideStream() {  // on an early error return the copies may still be in flight: wait for them
+    if (stream) cudaStreamSynchronize(stream);
+    if (ev) cudaEventDestroy(ev);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
 size_t ftle_host_workspace_bytes(int32_t dim, int64_t n_nodes, int64_t nnz, int32_t precision) {
   if ((dim != 2 && dim != 3) || n_nodes < 0 || nnz < 0) return 0;
   const size_t cb = (precision == FTLE_PREC_FP64 ? sizeof(double) : sizeof(float)) * (size_t)dim * (size_t)n_nodes;
@@ -469,12 +493,6 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
   off += align256(ftle_flowmap_bytes(dim, n_nodes, precision));
   void* ftle_dev = w + off;
   const size_t ob = (precision == FTLE_PREC_FP64 ? 8 : 4) * (size_t)n_nodes;
-  if (n_nodes > 0) {
-    FTLE_CUDA_CHECK(cudaMemcpyAsync(coords, coords_host, cb, cudaMemcpyHostToDevice, s));
-    FTLE_CUDA_CHECK(cudaMemcpyAsync(rp, row_ptr_host, sizeof(int32_t) * (size_t)(n_nodes + 1),
-                                    cudaMemcpyHostToDevice, s));
-  }
-  if (nnz > 0) FTLE_CUDA_CHECK(cudaMemcpyAsync(ci, col_idx_host, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
   ftle_mesh m;
   m.dim = dim;
   m.coord_fp64 = precision == FTLE_PREC_FP64 ? 1 : 0;
@@ -483,9 +501,31 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
   m.coords = coords;
   m.row_ptr = rp;
   m.col_idx = ci;
-  rc = ftle_compute(&m, flow, t0, T, dt, precision, phi, ftle_dev, nullptr, device_ws,
-                    align256(ftle_workspace_bytes(n_nodes)), opt, stream);
-  if (rc) return rc;
+  m.ell_width = 0;
+  m.reserved = 0;
+  m.ell_idx = nullptr;
+  int nsteps = 0;
+  if ((rc = check_mesh(&m)) || (rc = check_flow(flow, dim)) || (rc = check_time(T, dt, &nsteps))) return rc;
+  if (!isfinite(t0)) return fail(FTLE_EINVAL, "t0 must be finite");
+  const Launch L = resolve_launch(opt);
+  if ((rc = check_launch(L))) return rc;
+  // The neighbour lists are needed only once the flowmap is done, so they cross on a side stream
+  // while the advection (which needs the coordinates alone) runs.
+  SideStream side;
+  if ((rc = side.open(s))) return rc;
+  if (n_nodes > 0) {
+    FTLE_CUDA_CHECK(cudaMemcpyAsync(coords, coords_host, cb, cudaMemcpyHostToDevice, s));
+    FTLE_CUDA_CHECK(cudaMemcpyAsync(rp, row_ptr_host, sizeof(int32_t) * (size_t)(n_nodes + 1),
+                                    cudaMemcpyHostToDevice, side.stream));
+  }
+  if (nnz > 0)
+    FTLE_CUDA_CHECK(
+        cudaMemcpyAsync(ci, col_idx_host, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, side.stream));
+  if ((rc = run_advect(&m, flow, t0, T, dt, nsteps, precision, phi, nullptr, 0, L, s))) return rc;
+  if ((rc = side.join(s))) return rc;
+  FTLE_CUDA_CHECK(cudaMemsetAsync(device_ws, 0, sizeof(ftle_counters), s));
+  if ((rc = run_gradient(&m, phi, precision, T, ftle_dev, nullptr, device_ws, L, s))) return rc;
+  if ((rc = run_refine(&m, flow, t0, T, dt, nsteps, precision, phi, ftle_dev, nullptr, device_ws, L, s))) return rc;
   if (n_nodes > 0) FTLE_CUDA_CHECK(cudaMemcpyAsync(ftle_host, ftle_dev, ob, cudaMemcpyDeviceToHost, s));
   FTLE_CUDA_CHECK(cudaStreamSynchronize(s));
   return FTLE_OK;

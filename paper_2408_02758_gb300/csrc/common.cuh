@@ -164,6 +164,14 @@ __device__ __forceinline__ void ld_record256(const float4* p, float4& a, float4&
       : "l"(p));
 }
 
+// A neighbour index, read once: kept out of L1 so that the lines there serve the records that
+// neighbouring nodes share.
+__device__ __forceinline__ int ld_index(const int32_t* p) {
+  int v;
+  asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
 template <int DIM>
 __device__ __forceinline__ void load_record(const float4* rec, int64_t i, float* x, float* ph, float* pl) {
   float4 a, b;

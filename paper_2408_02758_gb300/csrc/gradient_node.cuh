@@ -58,9 +58,12 @@ __device__ __forceinline__ T sym3_lmax(T a00, T a01, T a02, T a11, T a12, T a22,
 
 // Float variant of sym3_lmax for the float kernel: constant reciprocals and a reciprocal square
 // root instead of divisions, and c = cos(acos(r)/3) as the largest root of 4c^3 - 3c = r (the
-// triple-angle identity) by three Newton steps from c0 = 1/2 + sqrt((1 + r)/6), which lies above
-// that root for every r in [-1, 1], so the steps descend onto it.  Near r = -1 the root is double
-// and the steps slow down; such nodes (1 + r <= kNearDoubleTop) take the FP64 path anyway.
+// triple-angle identity) by two Newton steps from c0 = 1/2 + sqrt(u/6) g(u), u = 1 + r.  The
+// factor g(u) = 1 - 0.16115366 u + 0.05104364 u^2 is a least-squares fit of the exact
+// (c - 1/2)/sqrt(u/6) over u in [0, 2] (g(0) = 1 keeps the leading term at the double root), so
+// c0 is within 1e-2 and two steps reach 2e-8 in exact arithmetic, below float rounding.  Near
+// r = -1 the root is double and the steps slow down; such nodes (1 + r <= kNearDoubleTop) take
+// the FP64 path anyway.
 __device__ __forceinline__ float sym3_lmax_f32(float a00, float a01, float a02, float a11, float a12, float a22,
                                                float& r_out) {
   const float q = (a00 + a11 + a22) * (1.0f / 3.0f);
@@ -78,9 +81,10 @@ __device__ __forceinline__ float sym3_lmax_f32(float a00, float a01, float a02, 
   float r = 0.5f * det * (rp * rp * rp);
   r = fminf(fmaxf(r, -1.0f), 1.0f);
   r_out = r;
-  float c = 0.5f + sqrtf((1.0f + r) * (1.0f / 6.0f));
+  const float u = 1.0f + r;
+  float c = fmaf(sqrtf(u * (1.0f / 6.0f)), fmaf(u, fmaf(u, 0.05104364f, -0.16115366f), 1.0f), 0.5f);
 #pragma unroll
-  for (int it = 0; it < 3; ++it) {
+  for (int it = 0; it < 2; ++it) {
     const float c2 = c * c;
     const float g = fmaf(c, fmaf(4.0f, c2, -3.0f), -r);
     c -= __fdividef(g, fmaf(12.0f, c2, -3.0f));
@@ -256,7 +260,7 @@ __device__ __forceinline__ bool grad_node_f32_rec(const GradArgs& a, int64_t i) 
   float xi[DIM], hi[DIM], li[DIM];
   float m[DIM * (DIM + 1) / 2] = {}, b[DIM * DIM] = {};
   load_record<DIM>(a.rec, i, xi, hi, li);
-  for (int e = rs; e < re; ++e) grad_accumulate_rec<DIM>(a.rec, __ldg(a.col_idx + e), xi, hi, li, m, b);
+  for (int e = rs; e < re; ++e) grad_accumulate_rec<DIM>(a.rec, ld_index(a.col_idx + e), xi, hi, li, m, b);
   return grad_finish_f32<DIM>(a, i, re - rs, m, b);
 }
 
@@ -266,7 +270,7 @@ __device__ __forceinline__ bool grad_node_f32_ell_rec(const GradArgs& a, int64_t
   int js[W > 0 ? W : 1];
   if constexpr (W > 0) {
 #pragma unroll
-    for (int s = 0; s < W; ++s) js[s] = __ldg(a.ell + (int64_t)s * n + i);
+    for (int s = 0; s < W; ++s) js[s] = ld_index(a.ell + (int64_t)s * n + i);
   }
   float xi[DIM], hi[DIM], li[DIM];
   float m[DIM * (DIM + 1) / 2] = {}, b[DIM * DIM] = {};
@@ -283,7 +287,7 @@ __device__ __forceinline__ bool grad_node_f32_ell_rec(const GradArgs& a, int64_t
     }
   } else {
     for (int s = 0; s < a.ell_width; ++s) {
-      const int j = __ldg(a.ell + (int64_t)s * n + i);
+      const int j = ld_index(a.ell + (int64_t)s * n + i);
       if (j >= 0) {
         grad_accumulate_rec<DIM>(a.rec, j, xi, hi, li, m, b);
         ++k;
