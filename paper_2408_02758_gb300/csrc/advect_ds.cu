@@ -1,7 +1,7 @@
 // Float-float RK4 re-advection of a short node list (the nodes the float gradient kernel flagged
 // and their neighbours).  Same scheme and stage times as k_advect, every operation in
-// float-float (~48-bit) arithmetic on the FP32 pipes; one node per lane, 32-thread blocks so the
-// few warps spread over the SM sub-partitions.  The double-gyre coefficient a(t) is tabulated
+// float-float (~48-bit) arithmetic on the FP32 pipes; one node per lane (two for the 2D double
+// gyre, three for the ABC flow), 32-thread blocks so the few warps spread over the SMs.  The double-gyre coefficient a(t) is tabulated
 // per block in double and split into float-float.
 #include "advect.cuh"
 #include "batch.cuh"
@@ -244,6 +244,85 @@ __global__ void __launch_bounds__(32) k_advect_ds_dg_pair(AdvArgs a) {
       }
     }
     ds_pair_store(a, K, i, active, x0, x);
+  }
+}
+
+// ABC flow with three lanes per node: lane d carries coordinate x_d and evaluates sin and cos
+// of it, and takes from its group the two values its velocity component needs,
+//   u_d = P_d sin x_{d+2} + Q_d cos x_{d+1}   (indices mod 3; (P, Q) = (A, C), (B, A), (C, B)),
+// four floats by shuffle.  A stage's step fraction is folded into (P, Q).  The node's three
+// float-float sines run on three lanes instead of interleaving in one, which cuts the chain a
+// lane issues per stage about threefold.  Ten nodes share a warp; lanes 30 and 31 integrate a
+// dummy group.
+struct DsTriConst {
+  dsf ph2, qh2, ph, qh, ph6, qh6;  // P and Q times h/2, h, h/6
+  dsf third;
+  int d, src_s, src_c;             // this lane's coordinate; lanes holding sin x_{d+2}, cos x_{d+1}
+};
+
+__device__ __forceinline__ DsTriConst ds_tri_const(const AdvArgs& a) {
+  DsTriConst K;
+  const int lane = threadIdx.x & 31, g = lane / 3;
+  K.d = lane - 3 * g;
+  K.src_s = 3 * g + (K.d + 2) % 3;  // lanes 30, 31 read lanes 32, 33, that is 0, 1 (shuffles wrap)
+  K.src_c = 3 * g + (K.d + 1) % 3;
+  const double P = a.p[K.d], Q = a.p[(K.d + 2) % 3];
+  K.ph2 = ds_from_double(P * 0.5 * a.h);
+  K.qh2 = ds_from_double(Q * 0.5 * a.h);
+  K.ph = ds_from_double(P * a.h);
+  K.qh = ds_from_double(Q * a.h);
+  K.ph6 = ds_from_double(P * a.h / 6.0);
+  K.qh6 = ds_from_double(Q * a.h / 6.0);
+  K.third = ds_from_double(1.0 / 3.0);
+  return K;
+}
+
+// This lane's velocity component at y (its own coordinate of the stage point) times a step
+// fraction, given as (P, Q) already scaled.
+__device__ __forceinline__ dsf ds_tri_abc_vel(const DsTriConst& K, const dsf& y, const dsf& p, const dsf& q) {
+  dsf sn, cs;
+  ds_sincos(y, sn, cs);
+  const dsf so = ds_make(__shfl_sync(0xffffffffu, sn.h, K.src_s), __shfl_sync(0xffffffffu, sn.l, K.src_s));
+  const dsf co = ds_make(__shfl_sync(0xffffffffu, cs.h, K.src_c), __shfl_sync(0xffffffffu, cs.l, K.src_c));
+  return ds_add(ds_mul_u(p, so), ds_mul_u(q, co));
+}
+
+// d1 = h/2 k1, d2 = h/2 k2, d3 = h k3, e4 = h/6 k4, and x + (d1 + 2 d2 + d3) / 3 + e4.
+__device__ __forceinline__ dsf ds_tri_abc_step(const DsTriConst& K, const dsf& x) {
+  const dsf d1 = ds_tri_abc_vel(K, x, K.ph2, K.qh2);
+  const dsf d2 = ds_tri_abc_vel(K, ds_add_u(x, d1), K.ph2, K.qh2);
+  const dsf d3 = ds_tri_abc_vel(K, ds_add_u(x, d2), K.ph, K.qh);
+  const dsf e4 = ds_tri_abc_vel(K, ds_add_u(x, d3), K.ph6, K.qh6);
+  const dsf sum = ds_add(ds_add(d1, d3), ds_make(2.0f * d2.h, 2.0f * d2.l));
+  return ds_add(x, ds_add(ds_mul(sum, K.third), e4));
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(32) k_advect_ds_abc_tri(AdvArgs a) {
+  const int64_t count = a.list ? (int64_t)*a.list_count : a.n;
+  const DsTriConst K = ds_tri_const(a);
+  const int g = (int)(threadIdx.x & 31) / 3;
+  // a.lanes (when set) caps the lanes of a block, as for the one-lane kernel: lanes / 3 nodes
+  const int cap = (a.lanes > 0 && a.lanes < (int)blockDim.x) ? a.lanes : (int)blockDim.x;
+  const int per_block = max(1, min(10, cap / 3));
+  for (int64_t base = (int64_t)blockIdx.x * per_block; base < count; base += (int64_t)gridDim.x * per_block) {
+    const int64_t slot = base + g;
+    const bool active = g < per_block && slot < count;
+    const int64_t i = active ? (a.list ? (int64_t)a.list[slot] : slot) : 0;
+    dsf x = ds_from_double(active ? (double)__ldg(reinterpret_cast<const CT*>(a.coords) + K.d * a.n_mesh + i) : 0.0);
+    const float x0 = x.h;
+    for (int k = 0; k < a.nsteps; ++k) x = ds_tri_abc_step(K, x);
+    // lane d = 0 of a group gathers the node's record from its two partners
+    const int lane = threadIdx.x & 31;
+    const float q0a = __shfl_sync(0xffffffffu, x0, lane + 1), q0b = __shfl_sync(0xffffffffu, x0, lane + 2);
+    const float qha = __shfl_sync(0xffffffffu, x.h, lane + 1), qhb = __shfl_sync(0xffffffffu, x.h, lane + 2);
+    const float qla = __shfl_sync(0xffffffffu, x.l, lane + 1), qlb = __shfl_sync(0xffffffffu, x.l, lane + 2);
+    if (!active) continue;
+    reinterpret_cast<float2*>(a.out)[K.d * a.n_mesh + i] = make_float2(x.h, x.l);
+    if (a.rec && K.d == 0) {
+      const float xs[3] = {x0, q0a, q0b}, ph[3] = {x.h, qha, qhb}, pl[3] = {x.l, qla, qlb};
+      store_record<3>(a.rec, i, xs, ph, pl);
+    }
   }
 }
 
@@ -581,7 +660,12 @@ int launch_advect_ds(int kind, int dim, bool coord64, const AdvArgs& args, int g
       k_advect_ds_dg_pair<double><<<2 * grid, block, smem, stream>>>(args);
     else
       k_advect_ds_dg_pair<float><<<2 * grid, block, smem, stream>>>(args);
-  } else if (kind == FTLE_FLOW_ABC && dim == 3) ds_dispatch<FTLE_FLOW_ABC, 3>(coord64, args, grid, block, smem, stream);
+  } else if (kind == FTLE_FLOW_ABC && dim == 3) {
+    if (coord64)
+      k_advect_ds_abc_tri<double><<<3 * grid, block, 0, stream>>>(args);
+    else
+      k_advect_ds_abc_tri<float><<<3 * grid, block, 0, stream>>>(args);
+  }
   else if (kind == FTLE_FLOW_LINEAR && dim == 2) ds_dispatch<FTLE_FLOW_LINEAR, 2>(coord64, args, grid, block, smem, stream);
   else if (kind == FTLE_FLOW_LINEAR && dim == 3) ds_dispatch<FTLE_FLOW_LINEAR, 3>(coord64, args, grid, block, smem, stream);
   else if (kind == FTLE_FLOW_SADDLE && dim == 2) ds_dispatch<FTLE_FLOW_SADDLE, 2>(coord64, args, grid, block, smem, stream);
