@@ -153,13 +153,23 @@ __device__ __forceinline__ DgDer dg_derivs32_rot(float piA, float as, float e1, 
 }
 
 // Segment table per half step: (a, b_l) of the forward kernel, sin(omega t), t cos(omega t).
+// The sine and cosine take dg_coef's reduction: u = omega t / pi in double, then sinpi and cospi
+// of u - rint(u) in float, so no double transcendental runs (GB300's FP64 rate is low, and every
+// block rebuilds the table for every segment).
 __device__ __forceinline__ void build_adj_table(const AdvArgs& a, float4* tab, int k0, int k1) {
   const double nu = a.p[2] / kPi;
   for (int m = threadIdx.x; m <= 2 * (k1 - k0); m += blockDim.x) {
     const int mm = 2 * k0 + m;
     const float2 c = dg_coef(a.p[1], nu, a.t0, 0.5 * a.h, mm);
     const double t = a.t0 + 0.5 * a.h * (double)mm;
-    tab[m] = make_float4(c.x, c.y, (float)sin(a.p[2] * t), (float)(t * cos(a.p[2] * t)));
+    const double u = nu * t, k = rint(u);
+    float sr, cr;
+    sincospif((float)(u - k), &sr, &cr);
+    if (((long long)k) & 1) {  // sin, cos(pi (k + r)) = (-1)^k sin, cos(pi r)
+      sr = -sr;
+      cr = -cr;
+    }
+    tab[m] = make_float4(c.x, c.y, sr, (float)t * cr);
   }
 }
 
