@@ -100,30 +100,32 @@ __global__ void __launch_bounds__(128) k_ftle_adjoint_gather(GradArgs g, const d
 // ---------------------------------------------------------------- 2. RK4 discrete adjoint
 
 struct DgDer {
-  float u0, u1;            // velocity
-  float j00, j01, j10, j11;  // du/dx
-  float pA0, pA1;          // du/dA
-  float q0, q1;            // du/deps = s q, du/domega = eps t c q
+  float u0, u1;              // velocity
+  float j01, j10, j11;       // du/dx (j00 = -j11: the flow is divergence-free)
+  float pA0, pA1;            // du/dA / pi
+  float q0, q1;              // du/deps = s q, du/domega = eps t c q
 };
 
 // Double-gyre velocity and derivatives at a point with abscissa x, from the slope f_x of the
 // stream function's argument and (sin, cos) of pi f and of pi y there; coefficient a = eps s.
+// The four products of the sines and cosines are formed once and shared.
 __device__ __forceinline__ DgDer dg_derivs_sc(float piA, float a, float fx, float x, float sf, float cf, float sy,
                                               float cy) {
   const float kPiF = 3.14159265358979323846f;
   DgDer d;
-  d.u0 = -piA * sf * cy;
-  d.u1 = piA * cf * sy * fx;
+  const float scy = sf * cy, ccy = cf * cy, csy = cf * sy, ssy = sf * sy;
+  const float t1 = csy * fx;
   const float pi2A = kPiF * piA;
-  d.j00 = -pi2A * cf * fx * cy;
-  d.j01 = pi2A * sf * sy;
-  d.j10 = piA * sy * fmaf(-kPiF * sf, fx * fx, cf * 2.0f * a);
-  d.j11 = pi2A * cf * cy * fx;
-  d.pA0 = -kPiF * sf * cy;
-  d.pA1 = kPiF * cf * sy * fx;
+  d.u0 = -piA * scy;
+  d.u1 = piA * t1;
+  d.j01 = pi2A * ssy;
+  d.j10 = piA * fmaf(-kPiF * ssy, fx * fx, csy * 2.0f * a);
+  d.j11 = pi2A * (ccy * fx);
+  d.pA0 = -scy;
+  d.pA1 = t1;
   const float g1 = fmaf(x, x, -2.0f * x), g2 = fmaf(2.0f, x, -2.0f);
-  d.q0 = -pi2A * cf * cy * g1;
-  d.q1 = piA * sy * fmaf(-kPiF * sf * g1, fx, cf * g2);
+  d.q0 = -pi2A * (ccy * g1);
+  d.q1 = piA * fmaf(-kPiF * ssy * g1, fx, csy * g2);
   return d;
 }
 
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adjoint_rk4(AdvArgs a, const floa
         const float kb4x = h6 * lam0, kb4y = h6 * lam1;
         float xbx = lam0, xby = lam1;
         auto stage = [&](const DgDer& d, float kbx, float kby, const float4& tc, float& ybx, float& yby) {
-          ybx = fmaf(d.j00, kbx, d.j10 * kby);
+          ybx = fmaf(-d.j11, kbx, d.j10 * kby);
           yby = fmaf(d.j01, kbx, d.j11 * kby);
           const float qk = fmaf(d.q0, kbx, d.q1 * kby);
           s0 = fmaf(d.pA0, kbx, fmaf(d.pA1, kby, s0));
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adjoint_rk4(AdvArgs a, const floa
         lam0 = xbx + ybx;
         lam1 = xby + yby;
       }
-      th0 += (double)s0;
+      th0 += kPi * (double)s0;  // the pA terms are du/dA / pi
       th1 += (double)s1;
       th2 += (double)s2;
     }
