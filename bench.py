@@ -235,6 +235,7 @@ def run_batched(args, world, rank, local):
     plan = ftle.BatchPlan(meshes, [w.flow for w in wl], [w.T for w in wl], 0.01, "fp32c", outs, ws, stream=sh)
     K, W = args.steps, args.warmup
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(W + K)]
+    dopt = ftle.make_options(defer_fp64=True)  # FP64 pass of the flagged nodes once, after refinement
     with torch.cuda.stream(stream):
         for k in range(W + K):
             if k == W:
@@ -317,6 +318,7 @@ def run_differentiable(args, world, rank, local):
     sh = stream.cuda_stream
     K, W = args.steps, args.warmup
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(W + K)]
+    dopt = ftle.make_options(defer_fp64=True)  # FP64 pass of the flagged nodes once, after refinement
     with torch.cuda.stream(stream):
         for k in range(W + K):
             if k == W:
@@ -332,8 +334,8 @@ def run_differentiable(args, world, rank, local):
             flush.fill_(float(k))
             e[2].record(stream)  # forward with checkpoints + backward
             ftle.ftle_advect(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi, ck, ce, stream=sh)
-            ftle.ftle_gradient_eig(dm, phi, "fp32c", w.T, out, None, ws, stream=sh)
-            ftle.ftle_refine(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi, out, None, ws, stream=sh)
+            ftle.ftle_gradient_eig(dm, phi, "fp32c", w.T, out, None, ws, options=dopt, stream=sh)
+            ftle.ftle_refine(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi, out, None, ws, options=dopt, stream=sh)
             ftle.ftle_backward(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi, ck, ce, wt, grad, bws, stream=sh)
             e[3].record(stream)
         torch.cuda.synchronize()
@@ -426,6 +428,9 @@ def main():
     sh = stream.cuda_stream
     K, W = args.steps, args.warmup
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(W + K)]
+    # the calls ftle_compute makes, timed one by one: the flagged nodes' FP64 pass runs once, after
+    # the re-advection (defer_fp64), as inside ftle_compute
+    opt = ftle.make_options(defer_fp64=True)
 
     def step(k):
         flush.fill_(float(k))
@@ -433,9 +438,9 @@ def main():
         e[0].record(stream)
         ftle.ftle_advect(dm, w.flow, 0.0, w.T, w.dt, prec, phi, stream=sh)
         e[1].record(stream)
-        ftle.ftle_gradient_eig(dm, phi, prec, w.T, out, None, ws, stream=sh)
+        ftle.ftle_gradient_eig(dm, phi, prec, w.T, out, None, ws, options=opt, stream=sh)
         e[2].record(stream)
-        ftle.ftle_refine(dm, w.flow, 0.0, w.T, w.dt, prec, phi, out, None, ws, stream=sh)
+        ftle.ftle_refine(dm, w.flow, 0.0, w.T, w.dt, prec, phi, out, None, ws, options=opt, stream=sh)
         e[3].record(stream)
 
     with torch.cuda.stream(stream):
@@ -522,7 +527,7 @@ def main():
                                     "(max SM clock of measured peaks)",
                      "flops_per_point_step": FLOPS_PER_POINT_STEP[kind], "ms": adv_ms,
                      "traffic": traffic.get("k_advect")},
-        "roofline_gradient": {"kernel": "gradient stage (float gradient kernel + FP64 fix-up + counter memset)", "bound": "hbm",
+        "roofline_gradient": {"kernel": "gradient stage (float gradient kernel + counter memset; the flagged nodes' FP64 pass runs in the refine stage)", "bound": "hbm",
                               "achieved": grad_bytes / (grad_ms / 1000.0) / 1e9, "peak": peaks.get("hbm_gbs"),
                               "unit": "GB/s", "frac": grad_bytes / (grad_ms / 1000.0) / 1e9 / peaks.get("hbm_gbs", 6800.0),
                               "bytes_per_launch": grad_bytes, "ms": grad_ms, "traffic": traffic.get("k_grad_f32")},

@@ -126,7 +126,13 @@ typedef struct ftle_options {
   int32_t grad_tile;      /* nodes per gradient tile (multiple of grad_block) */
   int32_t refine_lanes;   /* re-advection: active lanes per 32-thread block (1..32); fewer lanes
                              spread a short node list over more SM sub-partitions */
-  int32_t reserved[3];
+  int32_t defer_fp64;     /* 1: ftle_gradient_eig leaves the flagged nodes' FP64 pass to the
+                             ftle_refine that the caller runs next with these options, which
+                             recomputes those nodes after the re-advection anyway (their outputs
+                             stay NaN until then).  Ignored, and the pass runs, when ftle_refine
+                             would not refine (FP32, or refine_kappa < 0).  ftle_compute does
+                             this by itself. */
+  int32_t reserved[2];
 } ftle_options;
 
 /* ---------------------------------------------------------------------------------- sizes */
@@ -172,7 +178,8 @@ int ftle_advect(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double 
  *   workspace   device, ftle_workspace_bytes(n_nodes) bytes (required).
  * For FP32/FP32C the gradient runs in float; nodes where float loses the result (lambda_max
  * close to 1, two nearly equal top eigenvalues in 3D, an ill-conditioned M) are listed in the
- * workspace and recomputed in FP64 by a second kernel in the same call. */
+ * workspace and recomputed in FP64 by a second kernel in the same call (or, with
+ * ftle_options.defer_fp64, by the ftle_refine that follows). */
 int ftle_gradient_eig(const ftle_mesh* mesh, const void* flowmap, int32_t precision, double T,
                       void* ftle_out, double* lambda_out, void* workspace, size_t workspace_bytes,
                       const ftle_options* opt, void* stream);

@@ -33,8 +33,9 @@ class FTLEFunction(torch.autograd.Function):
         out = ftle.ftle_out_empty(n, precision)
         ws = ftle.workspace_empty(ftle.ftle_workspace_bytes(n))
         ftle.ftle_advect(mesh, flow, 0.0, T, dt, precision, phi, ckpt, ckpt_every)
-        ftle.ftle_gradient_eig(mesh, phi, precision, T, out, None, ws)
-        ftle.ftle_refine(mesh, flow, 0.0, T, dt, precision, phi, out, None, ws)
+        opt = ftle.make_options(defer_fp64=True)  # the FP64 pass runs once, after the re-advection
+        ftle.ftle_gradient_eig(mesh, phi, precision, T, out, None, ws, options=opt)
+        ftle.ftle_refine(mesh, flow, 0.0, T, dt, precision, phi, out, None, ws, options=opt)
         ctx.save_for_backward(phi, ckpt)
         ctx.mesh, ctx.flow, ctx.T, ctx.dt, ctx.precision, ctx.ckpt_every = mesh, flow, T, dt, precision, ckpt_every
         ctx.param_device, ctx.param_dtype = params.device, params.dtype

@@ -391,8 +391,9 @@ int enqueue_batch(const BatchPlanHost& P, cudaStream_t s) {
   if ((rc = launch_batch_grad(P.dim, pl, insts, reinterpret_cast<const BatchItem*>(w + P.L.grad_items),
                               (int)P.grad_items.size(), grad_next, hdr, flags, P.grad_grid, P.grad_block, s)))
     return rc;
-  if ((rc = launch_batch_grad_f64(P.dim, pl, insts, flags, &hdr->n_flagged, sms * 4, 128, s))) return rc;
-  if (!P.refine) return FTLE_OK;
+  // with the refinement on, the flagged nodes get their FP64 pass after the re-advection (which
+  // overwrites whatever a pass here would write), so only a batch without it runs one now
+  if (!P.refine) return launch_batch_grad_f64(P.dim, pl, insts, flags, &hdr->n_flagged, sms * 4, 128, s);
   FTLE_CUDA_CHECK(cudaMemsetAsync(w + P.L.bitmap, 0, sizeof(uint32_t) * (size_t)((P.L.total_nodes + 31) / 32 + 1), s));
   FTLE_CUDA_CHECK(cudaMemsetAsync(&hdr->n_degenerate, 0, sizeof(unsigned long long), s));
   if ((rc = launch_batch_mark(insts, flags, &hdr->n_flagged, marks, &hdr->n_readvected,

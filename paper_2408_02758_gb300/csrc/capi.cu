@@ -140,6 +140,7 @@ Launch resolve_launch(const ftle_options* opt) {
     if (opt->advect_blocks_per_sm > 0) L.advect_bps = opt->advect_blocks_per_sm;
     if (opt->grad_block > 0) L.grad_block = opt->grad_block;
     if (opt->refine_lanes > 0) L.refine_lanes = opt->refine_lanes;
+    L.defer_fp64 = opt->defer_fp64 != 0;
   }
   return L;
 }
@@ -242,8 +243,15 @@ float4* rec_ptr(const ftle_mesh* m, const void* phi, int precision) {
   return reinterpret_cast<float4*>(reinterpret_cast<char*>(const_cast<void*>(phi)) + rec_offset(m->dim, m->n_nodes));
 }
 
+bool refine_runs(const ftle_mesh* m, int precision, const Launch& L) {
+  return precision == FTLE_PREC_FP32C && m->n_nodes > 0 && L.refine_kappa >= 0;
+}
+
+// fixup: run the FP64 pass over the float kernel's flag list now.  ftle_compute leaves it to
+// run_refine when that runs, since the refinement recomputes the same list in FP64 after the
+// re-advection and overwrites every value a pass here would write.
 int run_gradient(const ftle_mesh* m, const void* phi, int precision, double T, void* ftle_out,
-                 double* lam_out, void* ws, const Launch& L, cudaStream_t s) {
+                 double* lam_out, void* ws, const Launch& L, cudaStream_t s, bool fixup) {
   if (m->n_nodes == 0) return FTLE_OK;
   GradArgs g = make_grad_args(m, phi, T, ftle_out, lam_out, ws, L);
   g.rec = rec_ptr(m, phi, precision);
@@ -255,7 +263,7 @@ int run_gradient(const ftle_mesh* m, const void* phi, int precision, double T, v
   }
   const int grid = grid_for(m->n_nodes, L.grad_block, 2048 / L.grad_block);
   int rc = launch_grad_f32(m->dim, phi_layout_of(precision), c64, g, grid, L.grad_block, s);
-  if (rc) return rc;
+  if (rc || !fixup) return rc;
   GradArgs f = g;
   f.list = g.flag_list;
   f.list_count = &g.hdr->n_flagged;
@@ -265,7 +273,7 @@ int run_gradient(const ftle_mesh* m, const void* phi, int precision, double T, v
 int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, double dt, int nsteps,
                int precision, void* phi, void* ftle_out, double* lam_out, void* ws, const Launch& L,
                cudaStream_t s) {
-  if (precision != FTLE_PREC_FP32C || m->n_nodes == 0 || L.refine_kappa < 0) return FTLE_OK;
+  if (!refine_runs(m, precision, L)) return FTLE_OK;
   const WsLayout W = ws_layout(m->n_nodes);
   char* w = reinterpret_cast<char*>(ws);
   ftle_counters* hdr = reinterpret_cast<ftle_counters*>(w + W.header);
@@ -395,7 +403,8 @@ int ftle_gradient_eig(const ftle_mesh* mesh, const void* flowmap, int32_t precis
   if ((rc = check_launch(L))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   FTLE_CUDA_CHECK(cudaMemsetAsync(workspace, 0, sizeof(ftle_counters), s));
-  return run_gradient(mesh, flowmap, precision, T, ftle_out, lambda_out, workspace, L, s);
+  return run_gradient(mesh, flowmap, precision, T, ftle_out, lambda_out, workspace, L, s,
+                      !(L.defer_fp64 && refine_runs(mesh, precision, L)));
 }
 
 int ftle_refine(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double T, double dt,
@@ -428,7 +437,9 @@ int ftle_compute(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = run_advect(mesh, flow, t0, T, dt, nsteps, precision, flowmap, nullptr, 0, L, s))) return rc;
   FTLE_CUDA_CHECK(cudaMemsetAsync(workspace, 0, sizeof(ftle_counters), s));
-  if ((rc = run_gradient(mesh, flowmap, precision, T, ftle_out, lambda_out, workspace, L, s))) return rc;
+  if ((rc = run_gradient(mesh, flowmap, precision, T, ftle_out, lambda_out, workspace, L, s,
+                         !refine_runs(mesh, precision, L))))
+    return rc;
   return run_refine(mesh, flow, t0, T, dt, nsteps, precision, flowmap, ftle_out, lambda_out, workspace, L, s);
 }
 
@@ -524,7 +535,8 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
   if ((rc = run_advect(&m, flow, t0, T, dt, nsteps, precision, phi, nullptr, 0, L, s))) return rc;
   if ((rc = side.join(s))) return rc;
   FTLE_CUDA_CHECK(cudaMemsetAsync(device_ws, 0, sizeof(ftle_counters), s));
-  if ((rc = run_gradient(&m, phi, precision, T, ftle_dev, nullptr, device_ws, L, s))) return rc;
+  if ((rc = run_gradient(&m, phi, precision, T, ftle_dev, nullptr, device_ws, L, s, !refine_runs(&m, precision, L))))
+    return rc;
   if ((rc = run_refine(&m, flow, t0, T, dt, nsteps, precision, phi, ftle_dev, nullptr, device_ws, L, s))) return rc;
   if (n_nodes > 0) FTLE_CUDA_CHECK(cudaMemcpyAsync(ftle_host, ftle_dev, ob, cudaMemcpyDeviceToHost, s));
   FTLE_CUDA_CHECK(cudaStreamSynchronize(s));

@@ -13,6 +13,7 @@ struct Launch {
   int advect_bps = 0;     // resident blocks per SM the advection grid is sized for (0: 2048/block)
   int grad_block = 256;
   int refine_lanes = 32;
+  bool defer_fp64 = false;
 };
 
 int check_mesh(const ftle_mesh* m);
@@ -43,8 +44,10 @@ GradArgs make_grad_args(const ftle_mesh* m, const void* phi, double T, void* ftl
 int run_advect(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, double dt, int nsteps,
                int precision, void* phi, void* ckpt, int ckpt_every, const Launch& L, cudaStream_t s);
 float4* rec_ptr(const ftle_mesh* m, const void* phi, int precision);
+// Whether run_refine re-advects and recomputes the flagged nodes for these arguments.
+bool refine_runs(const ftle_mesh* m, int precision, const Launch& L);
 int run_gradient(const ftle_mesh* m, const void* phi, int precision, double T, void* ftle_out,
-                 double* lam_out, void* ws, const Launch& L, cudaStream_t s);
+                 double* lam_out, void* ws, const Launch& L, cudaStream_t s, bool fixup);
 int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, double dt, int nsteps,
                int precision, void* phi, void* ftle_out, double* lam_out, void* ws, const Launch& L,
                cudaStream_t s);

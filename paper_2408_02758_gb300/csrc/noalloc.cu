@@ -60,5 +60,5 @@ extern "C" int ftle_gradient_eig_noalloc(const ftle_mesh* mesh, const void* flow
   if (ws_layout(mesh->n_nodes).flag_list != 256) return fail(FTLE_EINVAL, "unexpected workspace layout");
   cudaStream_t s = (cudaStream_t)stream;
   FTLE_CUDA_CHECK(cudaMemsetAsync(scratch, 0, sizeof(ftle_counters), s));
-  return run_gradient(mesh, flowmap, precision, T, ftle_out, lambda_out, scratch, L, s);
+  return run_gradient(mesh, flowmap, precision, T, ftle_out, lambda_out, scratch, L, s, true);
 }

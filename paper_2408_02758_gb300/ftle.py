@@ -42,7 +42,7 @@ class ftle_counters(Structure):
 class ftle_options(Structure):
     _fields_ = [("refine_kappa", c_double), ("advect_block", c_int32), ("advect_blocks_per_sm", c_int32),
                 ("grad_block", c_int32), ("grad_tile", c_int32), ("refine_lanes", c_int32),
-                ("reserved", c_int32 * 3)]
+                ("defer_fp64", c_int32), ("reserved", c_int32 * 2)]
 
 
 class FTLEError(RuntimeError):
@@ -153,9 +153,11 @@ def make_flow(flow) -> ftle_flow:
 
 
 def make_options(refine_kappa: float = 0.0, advect_block: int = 0, advect_blocks_per_sm: int = 0,
-                 grad_block: int = 0, grad_tile: int = 0, refine_lanes: int = 0) -> ftle_options:
+                 grad_block: int = 0, grad_tile: int = 0, refine_lanes: int = 0,
+                 defer_fp64: bool = False) -> ftle_options:
     o = ftle_options()
     o.refine_lanes = refine_lanes
+    o.defer_fp64 = int(bool(defer_fp64))
     o.refine_kappa = refine_kappa
     o.advect_block = advect_block
     o.advect_blocks_per_sm = advect_blocks_per_sm

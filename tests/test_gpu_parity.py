@@ -403,3 +403,35 @@ def test_gpu_csr_from_elements_rejects_bad_input(F):
     with pytest.raises(F.FTLEError) as e:
         F.ftle_csr_from_elements(4, el, 3)  # node 0 has 6 raw entries
     assert e.value.status == F.FTLE_ERANGE
+
+
+@pytest.mark.parametrize("preset,scale", [(1, 1 / 16), (2, 1 / 16)])
+def test_deferred_fp64_pass_gives_the_whole_path(F, preset, scale):
+    """With defer_fp64 the gradient call leaves its flagged nodes NaN for ftle_refine, which
+    recomputes them after the re-advection: the staged calls then equal ftle_compute (which
+    defers by itself) and the undeferred staged calls, bit for bit."""
+    import torch
+
+    w = I.preset(preset, scale=scale)
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    n = w.mesh.n_nodes
+    kappa = 0.3 if w.mesh.dim == 3 else 0.0  # a small 3D mesh flags nodes only with a wide test
+    outs = []
+    for defer in (True, False):
+        opt = F.make_options(defer_fp64=defer, refine_kappa=kappa)
+        phi = F.flowmap_empty(w.mesh.dim, n, "fp32c")
+        out = F.ftle_out_empty(n, "fp32c")
+        ws = F.workspace_empty(F.ftle_workspace_bytes(n))
+        F.ftle_advect(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi)
+        F.ftle_gradient_eig(dm, phi, "fp32c", w.T, out, None, ws, options=opt)
+        torch.cuda.synchronize()
+        flagged = F.ftle_read_counters(ws)["n_flagged"]
+        assert flagged > 0
+        n_nan = int(torch.isnan(out).sum())
+        assert (n_nan >= flagged) if defer else (n_nan < flagged)
+        F.ftle_refine(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi, out, None, ws, options=opt)
+        outs.append(out.cpu())
+    whole = F.compute(dm, w.flow, w.T, w.dt, "fp32c", options=F.make_options(refine_kappa=kappa)).cpu()
+    for o in outs:
+        assert torch.equal(torch.isnan(o), torch.isnan(whole))
+        assert torch.equal(o[~torch.isnan(o)], whole[~torch.isnan(whole)])
