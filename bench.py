@@ -369,6 +369,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--csr", action="store_true",
                     help="gradient over the CSR rows instead of the fixed-width neighbour list")
+    ap.add_argument("--stencil", action="store_true",
+                    help="gradient over the lattice's implicit neighbours (no neighbour index read)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="lattice axes scaled by this factor (smaller cases for profiler captures)")
     args = ap.parse_args()
@@ -418,6 +420,9 @@ def main():
     dm = ftle.DeviceMesh.from_mesh(w.mesh, device=dev)
     if not args.csr:
         dm.attach_ell()  # mesh preparation, outside the timed region (like the CSR lists)
+    if args.stencil:
+        dm.attach_stencil({I.AXIS: ftle.STENCIL_AXIS, I.TRI: ftle.STENCIL_TRI, I.KUHN: ftle.STENCIL_KUHN}[
+            w.mesh.meta["stencil"]], w.mesh.shape)
     prec = w.precision
     n = w.mesh.n_nodes
     phi = ftle.flowmap_empty(w.mesh.dim, n, prec, device=dev)
@@ -508,7 +513,7 @@ def main():
     nnz = w.mesh.nnz
     phi_b = 8 * w.mesh.dim * n if prec in ("fp32c", "fp64") else 4 * w.mesh.dim * n
     coord_b = w.mesh.coords.dtype.itemsize * w.mesh.dim * n
-    idx_b = 4 * (n + 1) + 4 * nnz if args.csr else 4 * dm.desc.ell_width * n
+    idx_b = 0 if args.stencil else (4 * (n + 1) + 4 * nnz if args.csr else 4 * dm.desc.ell_width * n)
     grad_bytes = idx_b + coord_b + phi_b + (8 if prec == "fp64" else 4) * n
     grad_ms = statistics.mean(t_grad)
     prof = ROOT / "profiles" / f"traffic_{w.name}.json"
@@ -519,7 +524,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": w.name, "nodes": n, "nnz": nnz, "steps_rk4": w.n_steps, "T": w.T, "dt": w.dt,
                    "precision": prec, "l2": "flushed between steps (320 MiB write, outside the events)",
-                   "neighbours": "CSR rows" if args.csr else f"fixed-width list, width {dm.desc.ell_width} (-1 padded)",
+                   "neighbours": ("implicit lattice stencil" if args.stencil else "CSR rows" if args.csr
+                                  else f"fixed-width list, width {dm.desc.ell_width} (-1 padded)"),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"kernel": "k_advect (RK4 flowmap)", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,

@@ -79,6 +79,18 @@ typedef enum ftle_flow_kind {
  *          ftle_out: float [n]. */
 typedef enum ftle_precision { FTLE_PREC_FP64 = 0, FTLE_PREC_FP32 = 1, FTLE_PREC_FP32C = 2 } ftle_precision;
 
+/* Neighbours implied by a structured lattice (ftle_mesh.stencil), offsets (ox, oy[, oz]):
+ *   FTLE_STENCIL_AXIS: +-e_a on every axis (4 in 2D, 6 in 3D);
+ *   FTLE_STENCIL_TRI (2D): +-e_x, +-e_y, +-(1, 1) (cells split along the (i,j)-(i+1,j+1) diagonal);
+ *   FTLE_STENCIL_KUHN (3D): +-e_a, +-(e_x + e_y), +-(e_y + e_z), +-(e_x + e_z), +-(1, 1, 1) (cubes
+ *   split into six tetrahedra around the main diagonal). */
+typedef enum ftle_stencil {
+  FTLE_STENCIL_NONE = 0,
+  FTLE_STENCIL_AXIS = 1,
+  FTLE_STENCIL_TRI = 2,
+  FTLE_STENCIL_KUHN = 3
+} ftle_stencil;
+
 typedef struct ftle_mesh {
   int32_t dim;            /* 2 or 3 */
   int32_t coord_fp64;     /* 0: coords are float, 1: coords are double */
@@ -95,6 +107,16 @@ typedef struct ftle_mesh {
   int32_t ell_width;      /* 0: no fixed-width list */
   int32_t reserved;       /* must be 0 */
   const int32_t* ell_idx; /* device [ell_width][n_nodes] or NULL */
+  /* Optional implicit neighbours of a structured lattice, the paper's regular access pattern
+   * (Section 2.2) without any list: node i = ix + grid[0] (iy + grid[1] iz) has as neighbours
+   * the stencil's offsets that stay inside the lattice, in ascending node order (the order of
+   * sorted CSR rows).  When stencil != FTLE_STENCIL_NONE the float gradient kernel reads no
+   * neighbour index (it takes precedence over ell_idx); the CSR arrays stay required for the FP64
+   * path, the refinement and the adjoint, and must list the same neighbours (the float and FP64
+   * paths would otherwise disagree).  grid[a] >= 2 on each axis, grid[2] = 1 in 2D, and
+   * grid[0] grid[1] grid[2] = n_nodes; FTLE_EINVAL otherwise. */
+  int32_t stencil;        /* ftle_stencil; 0: neighbours from the lists */
+  int32_t grid[3];        /* lattice nodes per axis, x fastest */
 } ftle_mesh;
 
 typedef struct ftle_flow {

@@ -84,6 +84,21 @@ int check_mesh(const ftle_mesh* m) {
   if (m->n_nodes > 0 && (!m->coords || !m->row_ptr)) return fail(FTLE_EINVAL, "mesh pointers are NULL");
   if (m->nnz > 0 && !m->col_idx) return fail(FTLE_EINVAL, "col_idx is NULL");
   if (m->ell_width < 0 || m->reserved != 0) return fail(FTLE_EINVAL, "ell_width < 0 or reserved != 0");
+  if (m->stencil != FTLE_STENCIL_NONE) {
+    if (m->stencil < FTLE_STENCIL_AXIS || m->stencil > FTLE_STENCIL_KUHN)
+      return fail(FTLE_EINVAL, "unknown stencil %d", m->stencil);
+    if ((m->stencil == FTLE_STENCIL_TRI && m->dim != 2) || (m->stencil == FTLE_STENCIL_KUHN && m->dim != 3))
+      return fail(FTLE_EINVAL, "stencil %d does not exist in %dD", m->stencil, m->dim);
+    int64_t prod = 1;
+    for (int a = 0; a < 3; ++a) {
+      const bool used = a < m->dim;
+      if ((used && m->grid[a] < 2) || (!used && m->grid[a] != 1))
+        return fail(FTLE_EINVAL, "stencil lattice: grid[%d] = %d (>= 2 on used axes, 1 otherwise)", a, m->grid[a]);
+      prod *= m->grid[a];
+    }
+    if (prod != m->n_nodes) return fail(FTLE_EINVAL, "stencil lattice has %lld nodes, mesh %lld", (long long)prod,
+                                        (long long)m->n_nodes);
+  }
   if (m->ell_width > 0 && m->n_nodes > 0 && !m->ell_idx) return fail(FTLE_EINVAL, "ell_width set without ell_idx");
   return FTLE_OK;
 }
@@ -219,6 +234,8 @@ GradArgs make_grad_args(const ftle_mesh* m, const void* phi, double T, void* ftl
   g.coords = m->coords;
   g.row_ptr = m->row_ptr;
   g.col_idx = m->col_idx;
+  g.stencil = m->stencil;
+  for (int q = 0; q < 3; ++q) g.grid[q] = (uint32_t)m->grid[q];
   if (m->ell_width > 0 && m->ell_idx) {
     g.ell = m->ell_idx;
     g.ell_width = m->ell_width;
@@ -515,6 +532,8 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
   m.ell_width = 0;
   m.reserved = 0;
   m.ell_idx = nullptr;
+  m.stencil = FTLE_STENCIL_NONE;
+  m.grid[0] = m.grid[1] = m.grid[2] = 0;
   int nsteps = 0;
   if ((rc = check_mesh(&m)) || (rc = check_flow(flow, dim)) || (rc = check_time(T, dt, &nsteps))) return rc;
   if (!isfinite(t0)) return fail(FTLE_EINVAL, "t0 must be finite");

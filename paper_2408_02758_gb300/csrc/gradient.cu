@@ -78,6 +78,25 @@ __global__ void __launch_bounds__(256) k_grad_f32_ell(GradArgs a) {
   }
 }
 
+// Float kernel over the implicit neighbours of a lattice stencil.
+template <int DIM, int ST, bool REC, int PL, typename CT>
+__global__ void __launch_bounds__(256) k_grad_f32_stencil(GradArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = a.n;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const bool flag = i < n && grad_node_f32_stencil<DIM, ST, REC, PL, CT>(a, i);
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask) {
+      const int leader = __ffs(mask) - 1;
+      unsigned long long basepos = 0;
+      if (lane == leader) basepos = atomicAdd(&a.hdr->n_flagged, (unsigned long long)__popc(mask));
+      basepos = __shfl_sync(0xffffffffu, basepos, leader);
+      if (flag) a.flag_list[basepos + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- double kernel
 
 // Every node (FTLE_PREC_FP64) or the nodes of a list, with lanes per node as the list's length
@@ -142,11 +161,29 @@ static void grad_f32_ell_dispatch(const GradArgs& a, int grid, int block, cudaSt
   }
 }
 
+template <int DIM, int ST, int PL>
+static void grad_f32_stencil_dispatch(bool rec, bool coord64, const GradArgs& a, int grid, int block, cudaStream_t s) {
+  if constexpr (PL == PHI32PAIR) {
+    if (rec) {
+      k_grad_f32_stencil<DIM, ST, true, PL, float><<<grid, block, 0, s>>>(a);
+      return;
+    }
+  }
+  if (coord64)
+    k_grad_f32_stencil<DIM, ST, false, PL, double><<<grid, block, 0, s>>>(a);
+  else
+    k_grad_f32_stencil<DIM, ST, false, PL, float><<<grid, block, 0, s>>>(a);
+}
+
 template <int DIM, int PL>
 static void grad_f32_dispatch(bool coord64, const GradArgs& a, int grid, int block, cudaStream_t s) {
   // gradient records exist for compensated flowmaps; they carry float coordinates
   const bool rec = PL == PHI32PAIR && a.rec && !coord64;
-  if (a.ell) {
+  if (a.stencil == FTLE_STENCIL_AXIS) {
+    grad_f32_stencil_dispatch<DIM, FTLE_STENCIL_AXIS, PL>(rec, coord64, a, grid, block, s);
+  } else if (a.stencil != FTLE_STENCIL_NONE) {  // TRI in 2D, KUHN in 3D (checked by the C-ABI)
+    grad_f32_stencil_dispatch<DIM, DIM == 2 ? FTLE_STENCIL_TRI : FTLE_STENCIL_KUHN, PL>(rec, coord64, a, grid, block, s);
+  } else if (a.ell) {
     if (rec)
       grad_f32_ell_dispatch<DIM, PL, float, true>(a, grid, block, s);
     else if (coord64)

@@ -26,6 +26,8 @@ struct GradArgs {
   const float4* rec;           // nullable: gradient records of a compensated flowmap (float coords)
   const int32_t* ell;          // nullable: fixed-width neighbour list [ell_width][n], -1 = none
   int ell_width;
+  int stencil;                 // ftle_stencil: implicit lattice neighbours (0: from the lists)
+  uint32_t grid[3];            // lattice nodes per axis when stencil != 0
   const int32_t* list;         // double kernel: nullable node list ...
   const unsigned long long* list_count;  // ... and its device-side length
 };

@@ -297,6 +297,69 @@ __device__ __forceinline__ bool grad_node_f32_ell_rec(const GradArgs& a, int64_t
   return grad_finish_f32<DIM>(a, i, k, m, b);
 }
 
+// Implicit neighbours of a lattice node (ftle_stencil): W offsets in ascending node order, which
+// is the order of the sorted CSR rows of the same mesh for lattices at least 2 nodes wide.
+template <int DIM, int ST>
+__device__ __forceinline__ constexpr int stencil_width() {
+  return ST == FTLE_STENCIL_AXIS ? 2 * DIM : (ST == FTLE_STENCIL_TRI ? 6 : 14);
+}
+
+template <int DIM, int ST>
+__device__ __forceinline__ void stencil_offset(int s, int& ox, int& oy, int& oz) {
+  if constexpr (DIM == 2 && ST == FTLE_STENCIL_AXIS) {
+    constexpr int t[4][2] = {{0, -1}, {-1, 0}, {1, 0}, {0, 1}};
+    ox = t[s][0], oy = t[s][1], oz = 0;
+  } else if constexpr (DIM == 2) {  // TRI
+    constexpr int t[6][2] = {{-1, -1}, {0, -1}, {-1, 0}, {1, 0}, {0, 1}, {1, 1}};
+    ox = t[s][0], oy = t[s][1], oz = 0;
+  } else if constexpr (ST == FTLE_STENCIL_AXIS) {
+    constexpr int t[6][3] = {{0, 0, -1}, {0, -1, 0}, {-1, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    ox = t[s][0], oy = t[s][1], oz = t[s][2];
+  } else {  // KUHN
+    constexpr int t[14][3] = {{-1, -1, -1}, {0, -1, -1}, {-1, 0, -1}, {0, 0, -1}, {-1, -1, 0},
+                              {0, -1, 0},   {-1, 0, 0},  {1, 0, 0},   {0, 1, 0},  {1, 1, 0},
+                              {0, 0, 1},    {1, 0, 1},   {0, 1, 1},   {1, 1, 1}};
+    ox = t[s][0], oy = t[s][1], oz = t[s][2];
+  }
+}
+
+// One node over the implicit neighbours of a lattice stencil: no neighbour index is read.  A
+// neighbour outside the lattice reads the node itself (dx = dphi = 0 adds exact zeros), as the
+// fixed-width list's padding does, so the unrolled loop has no branch and the accumulation order
+// over the real neighbours is the sorted CSR row's.
+template <int DIM, int ST, bool REC, int PL, typename CT>
+__device__ __forceinline__ bool grad_node_f32_stencil(const GradArgs& a, int64_t i) {
+  const uint32_t nx = a.grid[0], ny = a.grid[1], nz = a.grid[2];
+  const uint32_t u = (uint32_t)i, t = u / nx;
+  const uint32_t ix = u - t * nx, iy = DIM == 3 ? t % ny : t, iz = DIM == 3 ? t / ny : 0u;
+  const bool xm = ix > 0, xp = ix + 1 < nx, ym = iy > 0, yp = iy + 1 < ny, zm = iz > 0, zp = iz + 1 < nz;
+  const int sy = (int)nx, sz = (int)(nx * ny);
+  float m[DIM * (DIM + 1) / 2] = {}, b[DIM * DIM] = {};
+  float xr[DIM], hr[DIM], lr[DIM];  // record path: the node's coordinates and (hi, lo) flowmap
+  CT xc[DIM];
+  float2 pc[DIM];
+  if constexpr (REC)
+    load_record<DIM>(a.rec, i, xr, hr, lr);
+  else
+    grad_load_self<DIM, PL, CT>(a, i, xc, pc, m, b);
+  constexpr int W = stencil_width<DIM, ST>();
+  int k = 0;
+#pragma unroll
+  for (int s = 0; s < W; ++s) {
+    int ox, oy, oz;
+    stencil_offset<DIM, ST>(s, ox, oy, oz);
+    const bool ok = (ox < 0 ? xm : (ox > 0 ? xp : true)) && (oy < 0 ? ym : (oy > 0 ? yp : true)) &&
+                    (oz < 0 ? zm : (oz > 0 ? zp : true));
+    const int64_t j = ok ? i + (ox + oy * sy + oz * sz) : i;
+    if constexpr (REC)
+      grad_accumulate_rec<DIM>(a.rec, j, xr, hr, lr, m, b);
+    else
+      grad_accumulate<DIM, PL, CT>(a, j, xc, pc, m, b);
+    k += ok;
+  }
+  return grad_finish_f32<DIM>(a, i, k, m, b);
+}
+
 // Fixed-width list of a width without its own instantiation.
 template <int DIM, int PL, typename CT>
 __device__ __forceinline__ bool grad_node_f32_ell_any(const GradArgs& a, int64_t i) {

@@ -22,12 +22,13 @@ from . import _build
 
 PREC = {"fp64": 0, "fp32": 1, "fp32c": 2}
 FTLE_OK, FTLE_EINVAL, FTLE_ECUDA, FTLE_EWORKSPACE, FTLE_EUNSUPPORTED, FTLE_ERANGE, FTLE_ENOMEM = 0, -1, -2, -3, -4, -5, -6
+STENCIL_NONE, STENCIL_AXIS, STENCIL_TRI, STENCIL_KUHN = 0, 1, 2, 3  # ftle_stencil
 
 
 class ftle_mesh(Structure):
     _fields_ = [("dim", c_int32), ("coord_fp64", c_int32), ("n_nodes", c_int64), ("nnz", c_int64),
                 ("coords", c_void_p), ("row_ptr", c_void_p), ("col_idx", c_void_p), ("ell_width", c_int32),
-                ("reserved", c_int32), ("ell_idx", c_void_p)]
+                ("reserved", c_int32), ("ell_idx", c_void_p), ("stencil", c_int32), ("grid", c_int32 * 3)]
 
 
 class ftle_flow(Structure):
@@ -207,6 +208,22 @@ class DeviceMesh:
                                                             _stream(stream)))
         self.desc.ell_width = width
         self.desc.ell_idx = _ptr(self.ell)
+        return self
+
+    def attach_stencil(self, stencil: int, shape):
+        """Let the float gradient kernel take the neighbours implied by a structured lattice of
+        `shape` nodes (x fastest) instead of reading them: stencil is STENCIL_AXIS, STENCIL_TRI or
+        STENCIL_KUHN, and the CSR rows must list the same neighbours."""
+        shape = tuple(int(v) for v in shape)
+        self.desc.stencil = int(stencil)
+        for a in range(3):
+            self.desc.grid[a] = shape[a] if a < len(shape) else 1
+        return self
+
+    def detach_stencil(self):
+        self.desc.stencil = STENCIL_NONE
+        for a in range(3):
+            self.desc.grid[a] = 0
         return self
 
     def detach_ell(self):

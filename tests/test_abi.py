@@ -73,4 +73,21 @@ def test_status_strings_and_host_side_validation():
     assert L.ftle_flowmap_bytes(2, 10, 2) == 256 + 512 + 7 * 256 and L.ftle_flowmap_bytes(3, 10, 1) == 120
     assert L.ftle_flowmap_bytes(3, 10, 2) == 256 + 32 * 10
     assert L.ftle_checkpoint_bytes(2, 10, 2) == 160 and L.ftle_checkpoint_bytes(3, 10, 0) == 240
+    # implicit lattice neighbours: checked with the mesh, before any device work
+    m3 = ftle.ftle_mesh()
+    m3.dim, m3.n_nodes, m3.coords, m3.row_ptr = 3, 24, 256, 256  # pointers never dereferenced here
+    for stencil, grid, what in [(4, (2, 3, 4), b"unknown stencil"), (ftle.STENCIL_TRI, (2, 3, 4), b"does not exist"),
+                                (ftle.STENCIL_KUHN, (2, 3, 5), b"lattice has 30 nodes"),
+                                (ftle.STENCIL_KUHN, (1, 4, 6), b"grid[0] = 1")]:
+        m3.stencil = stencil
+        m3.grid[:] = grid
+        assert L.ftle_gradient_eig(ctypes.byref(m3), None, 2, 1.0, None, None, None, 0, None, None) == ftle.FTLE_EINVAL
+        assert what in L.ftle_last_error(), L.ftle_last_error()
+    m3.dim, m3.n_nodes, m3.stencil = 2, 6, ftle.STENCIL_TRI
+    m3.grid[:] = (2, 3, 2)  # the unused axis must be 1
+    assert L.ftle_gradient_eig(ctypes.byref(m3), None, 2, 1.0, None, None, None, 0, None, None) == ftle.FTLE_EINVAL
+    assert b"grid[2] = 2" in L.ftle_last_error()
+    m3.grid[:] = (2, 3, 1)  # a valid lattice: the call goes on and stops at the NULL flowmap
+    assert L.ftle_gradient_eig(ctypes.byref(m3), None, 2, 1.0, None, None, None, 0, None, None) == ftle.FTLE_EINVAL
+    assert b"flowmap" in L.ftle_last_error()
     assert L.ftle_workspace_bytes(1000) >= 8000

@@ -435,3 +435,25 @@ def test_deferred_fp64_pass_gives_the_whole_path(F, preset, scale):
     for o in outs:
         assert torch.equal(torch.isnan(o), torch.isnan(whole))
         assert torch.equal(o[~torch.isnan(o)], whole[~torch.isnan(whole)])
+
+
+@pytest.mark.parametrize("shape,stencil", [((37, 19), I.TRI), ((33, 17), I.AXIS), ((9, 7, 6), I.KUHN), ((9, 7, 6), I.AXIS)])
+@pytest.mark.parametrize("prec", ["fp32c", "fp32"])
+def test_implicit_stencil_matches_csr(F, shape, stencil, prec):
+    """Neighbours taken from the lattice (ftle_mesh.stencil, no index read) give the FTLE of the
+    CSR rows bit for bit: same neighbours, same order, padding slots adding exact zeros."""
+    import torch
+
+    dim = len(shape)
+    m = I.make_mesh(shape, (0,) * dim, (2,) + (1,) * (dim - 1), stencil, 0.3, 11)
+    flow = I.FlowSpec.double_gyre() if dim == 2 else I.FlowSpec.abc()
+    T = 5.0 if dim == 2 else 1.0
+    dm = F.DeviceMesh.from_mesh(m)
+    a = F.compute(dm, flow, T, 0.01, prec, want_lambda=True, return_all=True)
+    kind = {I.AXIS: F.STENCIL_AXIS, I.TRI: F.STENCIL_TRI, I.KUHN: F.STENCIL_KUHN}[stencil]
+    dm.attach_stencil(kind, shape)
+    b = F.compute(dm, flow, T, 0.01, prec, want_lambda=True, return_all=True)
+    for key in ("ftle", "lam"):
+        x, y = a[key].cpu(), b[key].cpu()
+        assert torch.equal(torch.isnan(x), torch.isnan(y)) and torch.equal(x[~torch.isnan(x)], y[~torch.isnan(y)]), key
+    assert F.ftle_read_counters(a["workspace"]) == F.ftle_read_counters(b["workspace"])

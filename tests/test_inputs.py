@@ -120,3 +120,29 @@ def test_element_lists_span_the_stencil_edges(shape, stencil):
                     pairs.add((int(a), int(b)))
     rows = np.repeat(np.arange(m.n_nodes), np.diff(m.row_ptr))
     assert pairs == set(zip(rows.tolist(), m.col_idx.tolist()))
+
+
+# The lattice neighbours of each stencil, as the C-ABI's ftle_stencil defines them (offsets in
+# (x, y[, z]), x fastest); every CSR row must be exactly the in-range offsets in ascending order.
+_STENCIL_OFFSETS = {
+    (2, I.AXIS): [(1, 0), (-1, 0), (0, 1), (0, -1)],
+    (2, I.TRI): [(1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1)],
+    (3, I.AXIS): [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)],
+    (3, I.KUHN): [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1), (1, 1, 0), (-1, -1, 0),
+                  (0, 1, 1), (0, -1, -1), (1, 0, 1), (-1, 0, -1), (1, 1, 1), (-1, -1, -1)],
+}
+
+
+@pytest.mark.parametrize("shape,stencil", [((5, 4), I.AXIS), ((5, 4), I.TRI), ((2, 2), I.TRI), ((4, 3, 3), I.AXIS),
+                                           ((4, 3, 3), I.KUHN), ((2, 2, 2), I.KUHN)])
+def test_csr_rows_are_the_implicit_stencil(shape, stencil):
+    """The implicit-stencil gradient path (ftle_mesh.stencil) takes a node's neighbours from the
+    lattice instead of the rows: the generated rows must be the in-range offsets, ascending."""
+    rp, ci = I.lattice_csr(shape, stencil)
+    dim = len(shape)
+    strides = [1, shape[0], shape[0] * (shape[1] if dim > 1 else 1)]
+    for i in range(int(np.prod(shape))):
+        idx = [i % shape[0], (i // shape[0]) % shape[1]] + ([i // (shape[0] * shape[1])] if dim == 3 else [])
+        want = sorted(sum(o[a] * strides[a] for a in range(dim)) + i for o in _STENCIL_OFFSETS[(dim, stencil)]
+                      if all(0 <= idx[a] + o[a] < shape[a] for a in range(dim)))
+        assert list(ci[rp[i]:rp[i + 1]]) == want, (i, idx)
