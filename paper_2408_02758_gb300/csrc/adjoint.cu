@@ -387,6 +387,7 @@ int ftle_backward(const ftle_mesh* mesh, const ftle_flow* flow, double t0, doubl
   g.col_idx = mesh->col_idx;
   g.phi = flowmap;
   g.inv_2absT = 1.0 / (2.0 * fabs(T));
+  g.inv_2absT32 = (float)g.inv_2absT;
   const int sms = device_sm_count() > 0 ? device_sm_count() : 1;
   if (precision == FTLE_PREC_FP32C)
     k_ftle_adjoint_node<float, PHI32PAIR><<<sms * 8, 128, 0, s>>>(g, dL_dftle, pa);

@@ -244,6 +244,7 @@ GradArgs make_grad_args(const ftle_mesh* m, const void* phi, double T, void* ftl
   g.ftle_out = ftle_out;
   g.lam_out = lam_out;
   g.inv_2absT = 1.0 / (2.0 * fabs(T));
+  g.inv_2absT32 = (float)g.inv_2absT;
   g.refine_kappa = (float)L.refine_kappa;
   g.hdr = reinterpret_cast<ftle_counters*>(w + W.header);
   g.flag_list = reinterpret_cast<int32_t*>(w + W.flag_list);

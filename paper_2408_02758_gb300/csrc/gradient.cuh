@@ -20,6 +20,8 @@ struct GradArgs {
   void* ftle_out;              // float [n] (double [n] when out64)
   double* lam_out;             // nullable
   double inv_2absT;            // 1 / (2 |T|)
+  float inv_2absT32;           // the same in float (a double-to-float conversion per node would
+                               // take GB300's narrow FP64 pipe)
   float refine_kappa;          // float kernel: flag nodes with ln(lambda_max) * h_i < refine_kappa
   ftle_counters* hdr;
   int32_t* flag_list;          // float kernel appends here

@@ -210,9 +210,9 @@ __device__ __forceinline__ bool grad_finish_f32(const GradArgs& a, int64_t i, in
   const bool sensitive =
       (a.refine_kappa >= 0.f) && !(lg * lg * trm >= a.refine_kappa * a.refine_kappa * (float)k);
   flag = flag || !(mu >= kMuFloor) || sensitive || !(lam == lam);
-  const float ftle = flag ? NAN : lg * (float)a.inv_2absT;
+  const float ftle = flag ? NAN : lg * a.inv_2absT32;
   reinterpret_cast<float*>(a.ftle_out)[i] = ftle;
-  if (a.lam_out) a.lam_out[i] = flag ? NAN : (double)lam;
+  if (a.lam_out) a.lam_out[i] = (double)(flag ? NAN : lam);
   return flag;
 }
 
