@@ -28,6 +28,8 @@ struct AdvArgs {
                                // scale, rounded once (compensated double gyre: -pi A, pi A; else 1)
   float hs_pi[2];              // double gyre: pi (h/2, h) pi A, the y angle per unit of carried v
   float habc[3][3];            // ABC: (h/2, h, h/6) times (A, B, C), rounded once
+  int rot_safe;                // ABC: no stage angle can exceed kRotMax (the host's bound on
+                               // |h| |u_q|), so the steps skip the angle check
   double p[12];                // flow parameters
   const int32_t* list;         // nullable: process list[0 .. *list_count)
   const unsigned long long* list_count;
@@ -202,12 +204,13 @@ __device__ __forceinline__ void dg_stage_rot(float as, float e1, float dg, float
 }
 
 // ABC stage two, three or four of the compensated step: stage one's (sin, cos) of x, y, z rotated
-// by the stage increments d (radians); the largest increment joins `mx`.  co = (A, B, C) times
+// by the stage increments d (radians); with CHECK the largest increment joins `mx`.  co = (A, B, C) times
 // the scale of the value returned (the next stage's increment, or h/6 k4).
+template <bool CHECK>
 __device__ __forceinline__ void abc_stage_rot(const float* co, const float* d, const float* s0, const float* c0,
                                               float& mx, float* k) {
   float s[3], c[3];
-  mx = fmaxf(mx, fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))));
+  if constexpr (CHECK) mx = fmaxf(mx, fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))));
 #pragma unroll
   for (int q = 0; q < 3; ++q) rotate_small(s0[q], c0[q], d[q], s[q], c[q]);
   k[0] = fmaf(co[0], s[2], co[2] * c[1]);
@@ -254,8 +257,10 @@ __device__ __forceinline__ void rk4_step_c_full(const AdvArgs& a, const Coef& c0
 
 // Advance one node by one classic RK4 step (stages at t, t + h/2, t + h/2, t + h, with the
 // coefficients c0, c1, c2 of those half steps).  P64 updates xd; P32 updates xh; P32C updates
-// the compensated pair (xh, xl), evaluating the velocity at compensated stage points.
-template <int KIND, int DIM, int PREC>
+// the compensated pair (xh, xl), evaluating the velocity at compensated stage points.  SAFE
+// (ABC with AdvArgs::rot_safe): every stage angle is known to be within kRotMax, so the rotated
+// stages run without the angle check; the result is the one the check would have let through.
+template <int KIND, int DIM, int PREC, bool SAFE = false>
 __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const Coef& c1, const Coef& c2,
                                          float* xh, float* xl, double* xd) {
   if constexpr (PREC == P64) {
@@ -320,10 +325,10 @@ __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const
     d1[0] = fmaf(a.habc[0][0], s0[2], a.habc[0][2] * c0v[1]);
     d1[1] = fmaf(a.habc[0][1], s0[0], a.habc[0][0] * c0v[2]);
     d1[2] = fmaf(a.habc[0][2], s0[1], a.habc[0][1] * c0v[0]);
-    abc_stage_rot(a.habc[0], d1, s0, c0v, mx, d2);
-    abc_stage_rot(a.habc[1], d2, s0, c0v, mx, d3);
-    abc_stage_rot(a.habc[2], d3, s0, c0v, mx, e4);
-    if (mx <= kRotMax) {
+    abc_stage_rot<!SAFE>(a.habc[0], d1, s0, c0v, mx, d2);
+    abc_stage_rot<!SAFE>(a.habc[1], d2, s0, c0v, mx, d3);
+    abc_stage_rot<!SAFE>(a.habc[2], d3, s0, c0v, mx, e4);
+    if (SAFE || mx <= kRotMax) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const float inc = fmaf(fmaf(2.f, d2[q], d1[q] + d3[q]), 1.0f / 3.0f, e4[q]);
@@ -368,7 +373,8 @@ __device__ __forceinline__ void split_state(float* xh, float* xl, const double* 
 
 // --------------------------------------------------------------------------------- kernel
 
-template <int KIND, int DIM, int PREC, int OUT, typename CT>
+// SAFE: the instantiation for AdvArgs::rot_safe (rk4_step's angle-check-free ABC step).
+template <int KIND, int DIM, int PREC, int OUT, typename CT, bool SAFE = false>
 __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kTable = (KIND == FTLE_FLOW_DOUBLE_GYRE);
@@ -421,7 +427,7 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
           const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
           const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
           const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
-          rk4_step<KIND, DIM, PREC>(a, c0, c1, c2, xh, xl, xd);
+          rk4_step<KIND, DIM, PREC, SAFE>(a, c0, c1, c2, xh, xl, xd);
           if (a.ckpt) {
             if (--ck_left == 0) {
               ck_left = a.ckpt_every;

@@ -12,7 +12,10 @@ int launch_advect_typed(int prec, int out, const AdvArgs& args, int grid, int bl
   } else if (prec == P32 && out == O32) {
     k_advect<KIND, DIM, P32, O32, CT><<<grid, block, smem, stream>>>(args);
   } else if (prec == P32C && out == O32PAIR) {
-    k_advect<KIND, DIM, P32C, O32PAIR, CT><<<grid, block, smem, stream>>>(args);
+    if (KIND == FTLE_FLOW_ABC && args.rot_safe)
+      k_advect<KIND, DIM, P32C, O32PAIR, CT, KIND == FTLE_FLOW_ABC><<<grid, block, smem, stream>>>(args);
+    else
+      k_advect<KIND, DIM, P32C, O32PAIR, CT><<<grid, block, smem, stream>>>(args);
   } else if (prec == P64 && out == O32PAIR) {
     k_advect<KIND, DIM, P64, O32PAIR, CT><<<grid, block, smem, stream>>>(args);
   } else {

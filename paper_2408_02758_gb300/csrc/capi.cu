@@ -213,6 +213,13 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
   const double hsc[3] = {0.5 * a.h, a.h, a.h / 6.0};
   for (int s = 0; s < 3; ++s)
     for (int q = 0; q < 3; ++q) a.habc[s][q] = (float)(hsc[s] * f->p[q]);
+  if (f->kind == FTLE_FLOW_ABC) {
+    // a stage increment of component q is a step fraction <= |h| times P_q sin + Q_q cos, with
+    // (P, Q) = (A, C), (B, A), (C, B); a margin covers the float rounding of the increments
+    const double A = fabs(f->p[0]), B = fabs(f->p[1]), C = fabs(f->p[2]);
+    const double bound = fabs(a.h) * fmax(A + C, fmax(B + A, C + B));
+    a.rot_safe = bound <= (double)kRotMax * (1.0 - 1e-5) ? 1 : 0;
+  }
   return a;
 }
 
