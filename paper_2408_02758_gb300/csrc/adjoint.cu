@@ -21,6 +21,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "advect.cuh"
 #include "capi_internal.cuh"
 #include "gradient_node.cuh"
@@ -189,6 +191,11 @@ __global__ void __launch_bounds__(kAdjBlock) k_adjoint_rk4(AdvArgs a, const floa
   const float piA = (float)(kPi * a.p[0]);
   const float eps = (float)a.p[1];
   float lam0 = active ? phibar[i] : 0.f, lam1 = active ? phibar[a.n_mesh + i] : 0.f;
+  // the forward kernel's choice between the checked and the unchecked step (dg_node_safe), so
+  // the recomputed states are the forward's
+  const bool safe = PREC == P32C && active &&
+                    dg_node_safe(a, (double)reinterpret_cast<const float*>(a.coords)[i],
+                                 (double)reinterpret_cast<const float*>(a.coords)[a.n_mesh + i]);
   double th0 = 0, th1 = 0, th2 = 0;
   const int nseg = (a.nsteps + ce - 1) / ce;
   for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -209,14 +216,20 @@ __global__ void __launch_bounds__(kAdjBlock) k_adjoint_rk4(AdvArgs a, const floa
         const float* c = reinterpret_cast<const float*>(slot);
         xh[0] = c[i]; xh[1] = c[a.n_mesh + i];
       }
-      for (int k = k0; k < k1; ++k) {
-        states[(k - k0) * blockDim.x + threadIdx.x] = make_float2(xh[0], xh[1]);
-        const int m = 2 * (k - k0);
-        Coef c0{tab[m].x, fmaf(-2.f, tab[m].x, 1.f), tab[m].y, 0.0};
-        Coef c1{tab[m + 1].x, fmaf(-2.f, tab[m + 1].x, 1.f), tab[m + 1].y, 0.0};
-        Coef c2{tab[m + 2].x, fmaf(-2.f, tab[m + 2].x, 1.f), tab[m + 2].y, 0.0};
-        rk4_step<FTLE_FLOW_DOUBLE_GYRE, 2, PREC>(a, c0, c1, c2, xh, xl, xd);
-      }
+      auto recompute = [&](auto unchecked) {
+        for (int k = k0; k < k1; ++k) {
+          states[(k - k0) * blockDim.x + threadIdx.x] = make_float2(xh[0], xh[1]);
+          const int m = 2 * (k - k0);
+          Coef c0{tab[m].x, fmaf(-2.f, tab[m].x, 1.f), tab[m].y, 0.0};
+          Coef c1{tab[m + 1].x, fmaf(-2.f, tab[m + 1].x, 1.f), tab[m + 1].y, 0.0};
+          Coef c2{tab[m + 2].x, fmaf(-2.f, tab[m + 2].x, 1.f), tab[m + 2].y, 0.0};
+          rk4_step<FTLE_FLOW_DOUBLE_GYRE, 2, PREC, decltype(unchecked)::value>(a, c0, c1, c2, xh, xl, xd);
+        }
+      };
+      if (safe)
+        recompute(std::true_type{});
+      else
+        recompute(std::false_type{});
       // reverse the segment's steps
       float s0 = 0.f, s1 = 0.f, s2 = 0.f;
       const float h = a.h32, h2 = a.h2_32, h6 = a.h6_32, h3 = 2.0f * a.h6_32;

@@ -4,6 +4,8 @@
 // live in a shared-memory table, rebuilt per chunk of steps.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace ftle {
@@ -28,8 +30,9 @@ struct AdvArgs {
                                // scale, rounded once (compensated double gyre: -pi A, pi A; else 1)
   float hs_pi[2];              // double gyre: pi (h/2, h) pi A, the y angle per unit of carried v
   float habc[3][3];            // ABC: (h/2, h, h/6) times (A, B, C), rounded once
-  int rot_safe;                // ABC: no stage angle can exceed kRotMax (the host's bound on
-                               // |h| |u_q|), so the steps skip the angle check
+  int rot_safe;                // no stage angle can exceed kRotMax (the host's bound on the
+                               // increments; for the double gyre, of nodes in [0, 2] x [0, 1]),
+                               // so the steps skip the angle check
   double p[12];                // flow parameters
   const int32_t* list;         // nullable: process list[0 .. *list_count)
   const unsigned long long* list_count;
@@ -187,6 +190,7 @@ __device__ __forceinline__ void comp_add(float xh, float d, float& s, float& e) 
 // kRotMax is recomputed in full (rk4_step_c_full).  The y increment arrives as kv with the
 // angle's scale hy_pi (pi times the increment's scale).  Returns the velocity without its
 // factors -pi A and pi A.
+template <bool CHECK>
 __device__ __forceinline__ void dg_stage_rot(float as, float e1, float dg, float dx, float kv_prev, float hy_pi,
                                              float sf, float cf, float sy, float cy, float& mx, float& ku,
                                              float& kv) {
@@ -194,7 +198,7 @@ __device__ __forceinline__ void dg_stage_rot(float as, float e1, float dg, float
   const float w = fmaf(as, e1 + dx, 1.0f);  // 1 + a_s (2 (x0 - 1) + dx)
   const float tf = kPiF * fmaf(dx, w, dg);
   const float ty = hy_pi * kv_prev;
-  mx = fmaxf(mx, fmaxf(fabsf(tf), fabsf(ty)));
+  if constexpr (CHECK) mx = fmaxf(mx, fmaxf(fabsf(tf), fabsf(ty)));
   float sfs, cfs, sys, cys;
   rotate_small(sf, cf, tf, sfs, cfs);
   rotate_small(sy, cy, ty, sys, cys);
@@ -258,8 +262,9 @@ __device__ __forceinline__ void rk4_step_c_full(const AdvArgs& a, const Coef& c0
 // Advance one node by one classic RK4 step (stages at t, t + h/2, t + h/2, t + h, with the
 // coefficients c0, c1, c2 of those half steps).  P64 updates xd; P32 updates xh; P32C updates
 // the compensated pair (xh, xl), evaluating the velocity at compensated stage points.  SAFE
-// (ABC with AdvArgs::rot_safe): every stage angle is known to be within kRotMax, so the rotated
-// stages run without the angle check; the result is the one the check would have let through.
+// (AdvArgs::rot_safe, and for the double gyre a node inside its invariant domain): every stage
+// angle is known to be within kRotMax, so the rotated stages run without the angle check (same
+// scheme; the rounding may differ from the checked step's, see dg_node_safe).
 template <int KIND, int DIM, int PREC, bool SAFE = false>
 __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const Coef& c1, const Coef& c2,
                                          float* xh, float* xl, double* xd) {
@@ -300,10 +305,10 @@ __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const
     const float g0 = xh[0] * (xh[0] - 2.0f);
     const float dg1 = (c1.a - c0.a) * g0, dg2 = (c2.a - c0.a) * g0;
     float k2u, k2v, k3u, k3v, k4u, k4v, mx = 0.0f;
-    dg_stage_rot(c1.a, e1, dg1, a.hs[0][0] * k1u, k1v, a.hs_pi[0], sf, cf, sy, cy, mx, k2u, k2v);
-    dg_stage_rot(c1.a, e1, dg1, a.hs[0][0] * k2u, k2v, a.hs_pi[0], sf, cf, sy, cy, mx, k3u, k3v);
-    dg_stage_rot(c2.a, e1, dg2, a.hs[0][1] * k3u, k3v, a.hs_pi[1], sf, cf, sy, cy, mx, k4u, k4v);
-    if (mx <= kRotMax) {
+    dg_stage_rot<!SAFE>(c1.a, e1, dg1, a.hs[0][0] * k1u, k1v, a.hs_pi[0], sf, cf, sy, cy, mx, k2u, k2v);
+    dg_stage_rot<!SAFE>(c1.a, e1, dg1, a.hs[0][0] * k2u, k2v, a.hs_pi[0], sf, cf, sy, cy, mx, k3u, k3v);
+    dg_stage_rot<!SAFE>(c2.a, e1, dg2, a.hs[0][1] * k3u, k3v, a.hs_pi[1], sf, cf, sy, cy, mx, k4u, k4v);
+    if (SAFE || mx <= kRotMax) {
       // the increment h/6 (k1 + 2 k2 + 2 k3 + k4) and the low part join in one rounding
       const float sum[2] = {fmaf(2.f, k2u + k3u, k1u + k4u), fmaf(2.f, k2v + k3v, k1v + k4v)};
 #pragma unroll
@@ -373,6 +378,16 @@ __device__ __forceinline__ void split_state(float* xh, float* xl, const double* 
 
 // --------------------------------------------------------------------------------- kernel
 
+// Whether a double-gyre node takes the unchecked steps: the host's angle bound holds (rot_safe)
+// and the node starts in the invariant domain [0, 2] x [0, 1] (x, y its initial coordinates).
+// The unchecked and the checked step may round differently (the compiler contracts their
+// products differently), so every kernel that advances a node (k_advect, k_batch_advect, the
+// adjoint's recomputation) decides by this function of the node alone, and their states agree
+// bit for bit.  A warp mixing both kinds of node runs the two loops one after the other.
+__device__ __forceinline__ bool dg_node_safe(const AdvArgs& a, double x, double y) {
+  return a.rot_safe && x >= 0.0 && x <= 2.0 && y >= 0.0 && y <= 1.0;
+}
+
 // SAFE: the instantiation for AdvArgs::rot_safe (rk4_step's angle-check-free ABC step).
 template <int KIND, int DIM, int PREC, int OUT, typename CT, bool SAFE = false>
 __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
@@ -402,6 +417,8 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
       x0[d] = xh[d];
     }
     if (a.ckpt && active) store_state<OUT, DIM>(a.ckpt, a.n_mesh, i, xh, xl, xd);
+    bool safe_node = false;
+    if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE && PREC == P32C) safe_node = dg_node_safe(a, xd[0], xd[1]);
     int ck_left = a.ckpt_every;
     int ck_slot = 1;
     constexpr bool kSegs = PREC == P32C && OUT == O32PAIR && DIM == 2;
@@ -422,22 +439,30 @@ __global__ void __launch_bounds__(256) k_advect(AdvArgs a) {
       for (int k = k0; k < k1;) {
         // steps up to the next run boundary (uniform across the block), then its state
         const int stop = (kSegs && a.seg) ? min(k1, next_seg) : k1;
-        for (; k < stop; ++k) {
-          const int m = 2 * (k - k0);
-          const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
-          const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
-          const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
-          rk4_step<KIND, DIM, PREC, SAFE>(a, c0, c1, c2, xh, xl, xd);
-          if (a.ckpt) {
-            if (--ck_left == 0) {
-              ck_left = a.ckpt_every;
-              split_state<PREC, DIM>(xh, xl, xd);
-              store_state<OUT, DIM>(reinterpret_cast<char*>(a.ckpt) + (int64_t)ck_slot * a.ckpt_stride_bytes,
-                                    a.n_mesh, i, xh, xl, xd);
-              ++ck_slot;
+        auto steps = [&](auto safe) {
+          for (; k < stop; ++k) {
+            const int m = 2 * (k - k0);
+            const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
+            const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
+            const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
+            rk4_step<KIND, DIM, PREC, decltype(safe)::value>(a, c0, c1, c2, xh, xl, xd);
+            if (a.ckpt) {
+              if (--ck_left == 0) {
+                ck_left = a.ckpt_every;
+                split_state<PREC, DIM>(xh, xl, xd);
+                store_state<OUT, DIM>(reinterpret_cast<char*>(a.ckpt) + (int64_t)ck_slot * a.ckpt_stride_bytes,
+                                      a.n_mesh, i, xh, xl, xd);
+                ++ck_slot;
+              }
             }
           }
-        }
+        };
+        if (SAFE)
+          steps(std::integral_constant<bool, SAFE>{});
+        else if (safe_node)
+          steps(std::true_type{});
+        else
+          steps(std::false_type{});
         if constexpr (kSegs) {
           if (a.seg && k == next_seg) {
             if (seg_slot < kSegments - 1)

@@ -13,6 +13,8 @@
 #include <numeric>
 #include <vector>
 
+#include <type_traits>
+
 #include "batch.cuh"
 #include "capi_internal.cuh"
 #include "gradient_node.cuh"
@@ -51,6 +53,9 @@ __global__ void __launch_bounds__(256) k_batch_advect(const BatchInst* __restric
       xl[d] = 0.f;
       x0[d] = xh[d];
     }
+    bool safe = false;
+    if constexpr (PREC == P32C && KIND == FTLE_FLOW_DOUBLE_GYRE) safe = dg_node_safe(a, xd[0], xd[1]);
+    if constexpr (PREC == P32C && KIND == FTLE_FLOW_ABC) safe = a.rot_safe != 0;
     const int nchunks = (a.nsteps + kAdvChunk - 1) / kAdvChunk;
     // run-boundary states of compensated 2D flowmaps (as k_advect stores them)
     constexpr bool kSegs = PREC == P32C && OUT == O32PAIR && DIM == 2;
@@ -69,13 +74,20 @@ __global__ void __launch_bounds__(256) k_batch_advect(const BatchInst* __restric
       if (!active) continue;
       for (int k = k0; k < k1;) {
         const int stop = (kSegs && a.seg) ? min(k1, next_seg) : k1;
-        for (; k < stop; ++k) {
-          const int m = 2 * (k - k0);
-          const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
-          const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
-          const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
-          rk4_step<KIND, DIM, PREC>(a, c0, c1, c2, xh, xl, xd);
-        }
+        auto steps = [&](auto safe) {
+          for (; k < stop; ++k) {
+            const int m = 2 * (k - k0);
+            const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
+            const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
+            const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
+            rk4_step<KIND, DIM, PREC, decltype(safe)::value>(a, c0, c1, c2, xh, xl, xd);
+          }
+        };
+        // the unchecked steps exactly where k_advect takes them (dg_node_safe; ABC: rot_safe)
+        if (safe)
+          steps(std::true_type{});
+        else
+          steps(std::false_type{});
         if constexpr (kSegs) {
           if (a.seg && k == next_seg) {
             if (seg_slot < kSegments - 1)

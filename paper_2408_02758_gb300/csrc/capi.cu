@@ -209,6 +209,15 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
   if (f->kind == FTLE_FLOW_DOUBLE_GYRE) {
     a.hs_pi[0] = (float)(kPi * 0.5 * a.h * kPi * f->p[0]);
     a.hs_pi[1] = (float)(kPi * a.h * kPi * f->p[0]);
+    // stage angles of a node in [0, 2] x [0, 1] (the invariant domain its trajectory keeps): the
+    // x increment is at most D = |h| pi |A|, so pi f moves by at most pi (D (1 + |eps| (2 + D)) +
+    // |eps| |omega| |h|) and pi y by at most pi |h| pi |A| (1 + 2 |eps| (1 + D)); a margin covers
+    // the float rounding of the angles and of positions a rounding off the walls
+    const double A = fabs(f->p[0]), eps = fabs(f->p[1]), om = fabs(f->p[2]), h = fabs(a.h);
+    const double D = h * kPi * A;
+    const double tf = kPi * (D * (1.0 + eps * (2.0 + D)) + eps * om * h);
+    const double ty = kPi * h * kPi * A * (1.0 + 2.0 * eps * (1.0 + D));
+    a.rot_safe = fmax(tf, ty) <= (double)kRotMax * (1.0 - 1e-3) ? 1 : 0;
   }
   const double hsc[3] = {0.5 * a.h, a.h, a.h / 6.0};
   for (int s = 0; s < 3; ++s)
@@ -218,7 +227,7 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
     // (P, Q) = (A, C), (B, A), (C, B); a margin covers the float rounding of the increments
     const double A = fabs(f->p[0]), B = fabs(f->p[1]), C = fabs(f->p[2]);
     const double bound = fabs(a.h) * fmax(A + C, fmax(B + A, C + B));
-    a.rot_safe = bound <= (double)kRotMax * (1.0 - 1e-5) ? 1 : 0;
+    a.rot_safe = bound <= (double)kRotMax * (1.0 - 1e-3) ? 1 : 0;
   }
   return a;
 }
