@@ -457,3 +457,31 @@ def test_implicit_stencil_matches_csr(F, shape, stencil, prec):
         x, y = a[key].cpu(), b[key].cpu()
         assert torch.equal(torch.isnan(x), torch.isnan(y)) and torch.equal(x[~torch.isnan(x)], y[~torch.isnan(y)]), key
     assert F.ftle_read_counters(a["workspace"]) == F.ftle_read_counters(b["workspace"])
+
+
+def test_double_gyre_nodes_inside_and_outside_the_domain(F):
+    """Nodes in [0, 2] x [0, 1] take the unchecked rotated steps, nodes outside the checked ones
+    (warps mixing both run the two loops); both follow the FP64 oracle's RK4, and the batched
+    kernel, deciding per node the same way, gives the same flowmap and FTLE bit for bit."""
+    import torch
+
+    m = I.make_mesh((45, 23), (-0.5, -0.25), (2.5, 1.25), I.TRI, 0.3, 17)
+    inside = (m.coords[0] >= 0) & (m.coords[0] <= 2) & (m.coords[1] >= 0) & (m.coords[1] <= 1)
+    assert 0 < inside.sum() < m.n_nodes
+    flow, T = I.FlowSpec.double_gyre(), 5.0
+    dm = F.DeviceMesh.from_mesh(m)
+    phi = F.flowmap_empty(2, m.n_nodes, "fp32c")
+    F.ftle_advect(dm, flow, 0.0, T, 0.01, "fp32c", phi)
+    ph = F.flowmap_pairs(phi, 2, m.n_nodes).double().cpu().numpy()
+    ph = ph[..., 0] + ph[..., 1]
+    ref = O.advect(flow.kind, flow.params, m.coords, T, 0.01)
+    err = np.abs(ph - ref) / np.maximum(1.0, np.abs(ref))
+    assert np.median(err[:, inside]) < 1e-6 and np.median(err[:, ~inside]) < 1e-6 and err.max() < 5e-3
+    single = F.compute(dm, flow, T, 0.01, "fp32c").cpu().double().numpy()
+    out = torch.full((m.n_nodes,), 7.0, dtype=torch.float32, device="cuda")
+    ws = F.workspace_empty(F.ftle_batch_workspace_bytes([dm], "fp32c"))
+    F.ftle_batch([dm], [flow], [T], 0.01, "fp32c", [out], ws)
+    b = out.cpu().double().numpy()
+    # identical except the float-float time coefficients of re-advected nodes (as in the batch tests)
+    same = (b == single) | (np.isnan(b) & np.isnan(single))
+    assert np.all(same | (np.abs(b - single) <= 1e-9 * np.abs(single)))
