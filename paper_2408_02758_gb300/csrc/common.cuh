@@ -260,16 +260,17 @@ __device__ __forceinline__ void dg_vel32c(float piA, float a, float bh, float bl
 
 // (sin, cos)(phi + th) from (s0, c0) = (sin, cos)(phi) by the angle-addition formulas, with the
 // small angle's sin th = th - th^3/6 and cos th - 1 = -th^2/2 + th^4/24 (Taylor).  For |th| <=
-// kRotMax the dropped terms are below th^5/120 <= 2.7e-9 and th^6/720 <= 2.2e-11; the small
-// corrections are formed first and added to s0, c0 with one rounding each.
+// kRotMax the dropped terms are below th^5/120 <= 2.7e-9 and th^6/720 <= 2.2e-11.  Each result
+// takes two fused steps, s0 + c0 sin th and then + s0 (cos th - 1): two roundings at the
+// result's scale (at most an ulp), for two FMA-pipe instructions instead of three.
 constexpr float kRotMax = 0.05f;
 
 __device__ __forceinline__ void rotate_small(float s0, float c0, float th, float& s, float& c) {
   const float t2 = th * th;
   const float st = fmaf(th * t2, -1.0f / 6.0f, th);
   const float cm = t2 * fmaf(t2, 1.0f / 24.0f, -0.5f);
-  s = s0 + fmaf(s0, cm, c0 * st);
-  c = c0 + fmaf(c0, cm, -(s0 * st));
+  s = fmaf(s0, cm, fmaf(c0, st, s0));
+  c = fmaf(c0, cm, fmaf(-s0, st, c0));
 }
 
 // --- double gyre, double precision
