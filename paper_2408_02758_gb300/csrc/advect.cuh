@@ -207,6 +207,18 @@ __device__ __forceinline__ void dg_stage_rot(float as, float e1, float dg, float
   kv = cfs * sys * fxs;
 }
 
+// The ABC velocity components times the step fractions folded into co = (A, B, C) h_s, from the
+// sines s and cosines c of x, y, z.
+__device__ __forceinline__ void abc_stage_k(const float* co, const float* s, const float* c, float* k) {
+  k[0] = fmaf(co[0], s[2], co[2] * c[1]);
+  k[1] = fmaf(co[1], s[0], co[0] * c[2]);
+  k[2] = fmaf(co[2], s[1], co[1] * c[0]);
+}
+
+// Largest stage-three angle difference the first-order turn takes (its dropped term, at most
+// kTinyMax^2 / 2 = 4.5e-8, stays at float rounding).
+constexpr float kTinyMax = 3e-4f;
+
 // ABC stage two, three or four of the compensated step: stage one's (sin, cos) of x, y, z rotated
 // by the stage increments d (radians); with CHECK the largest increment joins `mx`.  co = (A, B, C) times
 // the scale of the value returned (the next stage's increment, or h/6 k4).
@@ -217,9 +229,7 @@ __device__ __forceinline__ void abc_stage_rot(const float* co, const float* d, c
   if constexpr (CHECK) mx = fmaxf(mx, fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))));
 #pragma unroll
   for (int q = 0; q < 3; ++q) rotate_small(s0[q], c0[q], d[q], s[q], c[q]);
-  k[0] = fmaf(co[0], s[2], co[2] * c[1]);
-  k[1] = fmaf(co[1], s[0], co[0] * c[2]);
-  k[2] = fmaf(co[2], s[1], co[1] * c[0]);
+  abc_stage_k(co, s, c, k);
 }
 
 // One RK4 step of the compensated state with every stage's velocity evaluated in full at the
@@ -330,8 +340,27 @@ __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const
     d1[0] = fmaf(a.habc[0][0], s0[2], a.habc[0][2] * c0v[1]);
     d1[1] = fmaf(a.habc[0][1], s0[0], a.habc[0][0] * c0v[2]);
     d1[2] = fmaf(a.habc[0][2], s0[1], a.habc[0][1] * c0v[0]);
-    abc_stage_rot<!SAFE>(a.habc[0], d1, s0, c0v, mx, d2);
-    abc_stage_rot<!SAFE>(a.habc[1], d2, s0, c0v, mx, d3);
+    // stage two turns stage one's pairs by d1; stage three turns stage two's by d2 - d1 to first
+    // order (|d2 - d1| <= h^2/4 L U for a flow with Lipschitz constant L and speed bound U, so
+    // the dropped (d2 - d1)^2 / 2 stays near float rounding: kTinyMax); stage four turns stage
+    // one's by d3
+    float s2[3], c2v[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) rotate_small(s0[q], c0v[q], d1[q], s2[q], c2v[q]);
+    abc_stage_k(a.habc[0], s2, c2v, d2);
+    {
+      float s3[3], c3[3], dmax = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float dd = d2[q] - d1[q];
+        if constexpr (!SAFE) dmax = fmaxf(dmax, fabsf(dd));
+        s3[q] = fmaf(c2v[q], dd, s2[q]);
+        c3[q] = fmaf(-s2[q], dd, c2v[q]);
+      }
+      if constexpr (!SAFE)
+        mx = fmaxf(fmaxf(mx, fmaxf(fabsf(d1[0]), fmaxf(fabsf(d1[1]), fabsf(d1[2])))), dmax * (kRotMax / kTinyMax));
+      abc_stage_k(a.habc[1], s3, c3, d3);
+    }
     abc_stage_rot<!SAFE>(a.habc[2], d3, s0, c0v, mx, e4);
     if (SAFE || mx <= kRotMax) {
 #pragma unroll

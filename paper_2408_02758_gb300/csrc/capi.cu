@@ -225,9 +225,13 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
   if (f->kind == FTLE_FLOW_ABC) {
     // a stage increment of component q is a step fraction <= |h| times P_q sin + Q_q cos, with
     // (P, Q) = (A, C), (B, A), (C, B); a margin covers the float rounding of the increments
+    // and stage three's turn from stage two, d2 - d1 = h/2 (k2 - k1), is at most h^2/4 L U with
+    // the flow's speed bound U and Lipschitz constant L (max-norm row sums), both this same
+    // maximum pair sum for the ABC flow
     const double A = fabs(f->p[0]), B = fabs(f->p[1]), C = fabs(f->p[2]);
-    const double bound = fabs(a.h) * fmax(A + C, fmax(B + A, C + B));
-    a.rot_safe = bound <= (double)kRotMax * (1.0 - 1e-3) ? 1 : 0;
+    const double U = fmax(A + C, fmax(B + A, C + B));
+    const double bound = fabs(a.h) * U, tiny = 0.25 * a.h * a.h * U * U;
+    a.rot_safe = (bound <= (double)kRotMax * (1.0 - 1e-3) && tiny <= (double)kTinyMax * (1.0 - 1e-3)) ? 1 : 0;
   }
   return a;
 }
