@@ -190,6 +190,43 @@ __device__ __forceinline__ void comp_add(float xh, float d, float& s, float& e) 
 // kRotMax is recomputed in full (rk4_step_c_full).  The y increment arrives as kv with the
 // angle's scale hy_pi (pi times the increment's scale).  Returns the velocity without its
 // factors -pi A and pi A.
+// Double gyre stages two and three of the unchecked step (nodes in the invariant domain).  Stage
+// two turns stage one's pairs as dg_stage_rot does, but keeps the turn's corrections apart
+// (sin = s0 + ds); stage three turns stage two's pairs by the angle difference (tf3 - tf2,
+// ty3 - ty2: about 1e-4 at dt = 0.01, so the dropped square is near 5e-9) to first order, adding
+// that to the kept correction before the one rounding onto s0.  Stage three thus costs a few
+// fused operations instead of a full turn, at stage two's accuracy (measured: the same error bins
+// as turning every stage from stage one).  Returns the velocities without -pi A and pi A.
+__device__ __forceinline__ void dg_stages23(float as, float e1, float dg, float hs, float hy_pi, float k1u, float k1v,
+                                            float sf, float cf, float sy, float cy, float& k2u, float& k2v,
+                                            float& k3u, float& k3v) {
+  const float kPiF = 3.14159265358979323846f;
+  const float dx2 = hs * k1u;
+  const float w2 = fmaf(as, e1 + dx2, 1.0f);
+  const float tf2 = kPiF * fmaf(dx2, w2, dg), ty2 = hy_pi * k1v;
+  float dsf, dcf, dsy, dcy;
+  {
+    const float t2 = tf2 * tf2, st = fmaf(tf2 * t2, -1.0f / 6.0f, tf2), cm = t2 * fmaf(t2, 1.0f / 24.0f, -0.5f);
+    dsf = fmaf(sf, cm, cf * st);
+    dcf = fmaf(cf, cm, -(sf * st));
+  }
+  {
+    const float t2 = ty2 * ty2, st = fmaf(ty2 * t2, -1.0f / 6.0f, ty2), cm = t2 * fmaf(t2, 1.0f / 24.0f, -0.5f);
+    dsy = fmaf(sy, cm, cy * st);
+    dcy = fmaf(cy, cm, -(sy * st));
+  }
+  const float sf2 = sf + dsf, cf2 = cf + dcf, sy2 = sy + dsy, cy2 = cy + dcy;
+  k2u = sf2 * cy2;
+  k2v = cf2 * sy2 * fmaf(as, dx2, w2);
+  const float dx3 = hs * k2u;
+  const float w3 = fmaf(as, e1 + dx3, 1.0f);
+  const float df = kPiF * fmaf(dx3, w3, dg) - tf2, dy = hy_pi * k2v - ty2;
+  const float sf3 = sf + fmaf(cf2, df, dsf), cf3 = cf + fmaf(-sf2, df, dcf);
+  const float sy3 = sy + fmaf(cy2, dy, dsy), cy3 = cy + fmaf(-sy2, dy, dcy);
+  k3u = sf3 * cy3;
+  k3v = cf3 * sy3 * fmaf(as, dx3, w3);
+}
+
 template <bool CHECK>
 __device__ __forceinline__ void dg_stage_rot(float as, float e1, float dg, float dx, float kv_prev, float hy_pi,
                                              float sf, float cf, float sy, float cy, float& mx, float& ku,
@@ -315,8 +352,12 @@ __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const
     const float g0 = xh[0] * (xh[0] - 2.0f);
     const float dg1 = (c1.a - c0.a) * g0, dg2 = (c2.a - c0.a) * g0;
     float k2u, k2v, k3u, k3v, k4u, k4v, mx = 0.0f;
-    dg_stage_rot<!SAFE>(c1.a, e1, dg1, a.hs[0][0] * k1u, k1v, a.hs_pi[0], sf, cf, sy, cy, mx, k2u, k2v);
-    dg_stage_rot<!SAFE>(c1.a, e1, dg1, a.hs[0][0] * k2u, k2v, a.hs_pi[0], sf, cf, sy, cy, mx, k3u, k3v);
+    if constexpr (SAFE) {
+      dg_stages23(c1.a, e1, dg1, a.hs[0][0], a.hs_pi[0], k1u, k1v, sf, cf, sy, cy, k2u, k2v, k3u, k3v);
+    } else {
+      dg_stage_rot<!SAFE>(c1.a, e1, dg1, a.hs[0][0] * k1u, k1v, a.hs_pi[0], sf, cf, sy, cy, mx, k2u, k2v);
+      dg_stage_rot<!SAFE>(c1.a, e1, dg1, a.hs[0][0] * k2u, k2v, a.hs_pi[0], sf, cf, sy, cy, mx, k3u, k3v);
+    }
     dg_stage_rot<!SAFE>(c2.a, e1, dg2, a.hs[0][1] * k3u, k3v, a.hs_pi[1], sf, cf, sy, cy, mx, k4u, k4v);
     if (SAFE || mx <= kRotMax) {
       // the increment h/6 (k1 + 2 k2 + 2 k3 + k4) and the low part join in one rounding
