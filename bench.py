@@ -33,14 +33,18 @@ UNIT = "points/s"
 FLUSH_BYTES = 320 << 20
 
 
-# Algorithmic FP32 flops of one compensated RK4 step per node (FMA = 2 flops; one sincospi or
-# sincos counted as 20 flops: argument reduction plus degree-7/8 minimax polynomials).
+# Algorithmic FP32 flops of one compensated RK4 step per node as the kernels take it (FMA = 2
+# flops; one sincospi or sincos counted as 20 flops: argument reduction plus degree-7/8 minimax
+# polynomials; a small-angle rotation of a (sin, cos) pair 15).
 #   double gyre: stage one 74 (error-free f 17, two sincospi 40, first-order corrections 10,
-#                slope and velocity 7), per-step terms 6, stages two to four 3 x 43 (two
-#                small-angle rotations 30, angles 7, slope 2, increment 1, velocity 3), update 18
-#   ABC:         stage one 87 (three compensated sincos 78, increments 9), stages two to four
-#                3 x 54 (three rotations 45, increments 9), update 27
-FLOPS_PER_POINT_STEP = {"dg": 227, "abc": 276}
+#                slope and velocity 7), per-step terms 6, stages two and four 2 x 43 (two
+#                rotations 30, angles 7, slope 2, increment 1, velocity 3), stage three 27
+#                (angles and their differences 11, four first-order turns 12, slope and
+#                velocity 4), update 18
+#   ABC:         stage one 87 (three compensated sincos 78, increments 9), stages two and four
+#                2 x 54 (three rotations 45, increments 9), stage three 24 (three first-order
+#                turns 15, increments 9), update 27
+FLOPS_PER_POINT_STEP = {"dg": 211, "abc": 246}
 
 
 def peak_fp32_tflops(sms: int, mhz: float) -> float:
