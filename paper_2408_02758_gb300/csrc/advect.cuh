@@ -190,10 +190,32 @@ __device__ __forceinline__ void comp_add(float xh, float d, float& s, float& e) 
 // kRotMax is recomputed in full (rk4_step_c_full).  The y increment arrives as kv with the
 // angle's scale hy_pi (pi times the increment's scale).  Returns the velocity without its
 // factors -pi A and pi A.
+template <bool CHECK>
+__device__ __forceinline__ void dg_stage_rot(float as, float e1, float dg, float dx, float kv_prev, float hy_pi,
+                                             float sf, float cf, float sy, float cy, float& mx, float& ku,
+                                             float& kv) {
+  const float kPiF = 3.14159265358979323846f;
+  const float w = fmaf(as, e1 + dx, 1.0f);  // 1 + a_s (2 (x0 - 1) + dx)
+  const float tf = kPiF * fmaf(dx, w, dg);
+  const float ty = hy_pi * kv_prev;
+  if constexpr (CHECK) mx = fmaxf(mx, fmaxf(fabsf(tf), fabsf(ty)));
+  float sfs, cfs, sys, cys;
+  rotate_small(sf, cf, tf, sfs, cfs);
+  rotate_small(sy, cy, ty, sys, cys);
+  const float fxs = fmaf(as, dx, w);  // f_s'(x0 + dx) = 1 + 2 a_s (x0 + dx - 1)
+  ku = sfs * cys;
+  kv = cfs * sys * fxs;
+}
+
+// Largest stage-three angle difference the first-order turns of the unchecked steps take (the
+// dropped term, at most kTinyMax^2 / 2 = 4.5e-8, stays at float rounding).
+constexpr float kTinyMax = 3e-4f;
+
 // Double gyre stages two and three of the unchecked step (nodes in the invariant domain).  Stage
 // two turns stage one's pairs as dg_stage_rot does, but keeps the turn's corrections apart
 // (sin = s0 + ds); stage three turns stage two's pairs by the angle difference (tf3 - tf2,
-// ty3 - ty2: about 1e-4 at dt = 0.01, so the dropped square is near 5e-9) to first order, adding
+// ty3 - ty2, which the host bounds by kTinyMax for these steps: 1.4e-4 at dt = 0.01 on the
+// default workload, so the dropped square stays below 1e-8) to first order, adding
 // that to the kept correction before the one rounding onto s0.  Stage three thus costs a few
 // fused operations instead of a full turn, at stage two's accuracy (measured: the same error bins
 // as turning every stage from stage one).  Returns the velocities without -pi A and pi A.
@@ -227,23 +249,6 @@ __device__ __forceinline__ void dg_stages23(float as, float e1, float dg, float 
   k3v = cf3 * sy3 * fmaf(as, dx3, w3);
 }
 
-template <bool CHECK>
-__device__ __forceinline__ void dg_stage_rot(float as, float e1, float dg, float dx, float kv_prev, float hy_pi,
-                                             float sf, float cf, float sy, float cy, float& mx, float& ku,
-                                             float& kv) {
-  const float kPiF = 3.14159265358979323846f;
-  const float w = fmaf(as, e1 + dx, 1.0f);  // 1 + a_s (2 (x0 - 1) + dx)
-  const float tf = kPiF * fmaf(dx, w, dg);
-  const float ty = hy_pi * kv_prev;
-  if constexpr (CHECK) mx = fmaxf(mx, fmaxf(fabsf(tf), fabsf(ty)));
-  float sfs, cfs, sys, cys;
-  rotate_small(sf, cf, tf, sfs, cfs);
-  rotate_small(sy, cy, ty, sys, cys);
-  const float fxs = fmaf(as, dx, w);  // f_s'(x0 + dx) = 1 + 2 a_s (x0 + dx - 1)
-  ku = sfs * cys;
-  kv = cfs * sys * fxs;
-}
-
 // The ABC velocity components times the step fractions folded into co = (A, B, C) h_s, from the
 // sines s and cosines c of x, y, z.
 __device__ __forceinline__ void abc_stage_k(const float* co, const float* s, const float* c, float* k) {
@@ -251,10 +256,6 @@ __device__ __forceinline__ void abc_stage_k(const float* co, const float* s, con
   k[1] = fmaf(co[1], s[0], co[0] * c[2]);
   k[2] = fmaf(co[2], s[1], co[1] * c[0]);
 }
-
-// Largest stage-three angle difference the first-order turn takes (its dropped term, at most
-// kTinyMax^2 / 2 = 4.5e-8, stays at float rounding).
-constexpr float kTinyMax = 3e-4f;
 
 // ABC stage two, three or four of the compensated step: stage one's (sin, cos) of x, y, z rotated
 // by the stage increments d (radians); with CHECK the largest increment joins `mx`.  co = (A, B, C) times

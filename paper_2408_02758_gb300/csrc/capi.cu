@@ -217,7 +217,18 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
     const double D = h * kPi * A;
     const double tf = kPi * (D * (1.0 + eps * (2.0 + D)) + eps * om * h);
     const double ty = kPi * h * kPi * A * (1.0 + 2.0 * eps * (1.0 + D));
-    a.rot_safe = fmax(tf, ty) <= (double)kRotMax * (1.0 - 1e-3) ? 1 : 0;
+    // stage three turns stage two's pairs by the angle differences to first order: with the
+    // half-step increment D2 = D / 2 and the stage-two angle bound S2 (pi f and pi y together),
+    // |d pi f| <= pi D2 S2 (1 + |eps| (2 + 2 D2)) (dg cancels, k_u moves by at most the angles)
+    // and |d pi y| <= pi D2 pi ((1 + 2 |eps| (1 + D2)) S2 + |eps| |omega| |h| + 2 |eps| D2)
+    // (k_v adds the slope's change), each to stay within kTinyMax
+    const double D2 = 0.5 * D;
+    const double S2 = kPi * (D2 * (1.0 + eps * (2.0 + D2)) + 0.5 * eps * om * h) +
+                      kPi * D2 * (1.0 + 2.0 * eps * (1.0 + D2));
+    const double df = kPi * D2 * S2 * (1.0 + eps * (2.0 + 2.0 * D2));
+    const double dy = kPi * D2 * ((1.0 + 2.0 * eps * (1.0 + D2)) * S2 + eps * om * h + 2.0 * eps * D2);
+    a.rot_safe = (fmax(tf, ty) <= (double)kRotMax * (1.0 - 1e-3) &&
+                  fmax(df, dy) <= (double)kTinyMax * (1.0 - 1e-3)) ? 1 : 0;
   }
   const double hsc[3] = {0.5 * a.h, a.h, a.h / 6.0};
   for (int s = 0; s < 3; ++s)
