@@ -199,12 +199,11 @@ __device__ __forceinline__ void dg_stage_rot(float as, float e1, float dg, float
   const float tf = kPiF * fmaf(dx, w, dg);
   const float ty = hy_pi * kv_prev;
   if constexpr (CHECK) mx = fmaxf(mx, fmaxf(fabsf(tf), fabsf(ty)));
-  float sfs, cfs, sys, cys;
-  rotate_small(sf, cf, tf, sfs, cfs);
-  rotate_small(sy, cy, ty, sys, cys);
+  float2 s, c;  // lanes: pi f, pi y
+  rotate_small2(make_float2(sf, sy), make_float2(cf, cy), make_float2(tf, ty), s, c);
   const float fxs = fmaf(as, dx, w);  // f_s'(x0 + dx) = 1 + 2 a_s (x0 + dx - 1)
-  ku = sfs * cys;
-  kv = cfs * sys * fxs;
+  ku = s.x * c.y;
+  kv = c.x * s.y * fxs;
 }
 
 // Largest stage-three angle difference the first-order turns of the unchecked steps take (the
@@ -387,8 +386,15 @@ __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const
     // the dropped (d2 - d1)^2 / 2 stays near float rounding: kTinyMax); stage four turns stage
     // one's by d3
     float s2[3], c2v[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) rotate_small(s0[q], c0v[q], d1[q], s2[q], c2v[q]);
+    {  // x and y in one paired rotation, z alone
+      float2 sp, cp;
+      rotate_small2(make_float2(s0[0], s0[1]), make_float2(c0v[0], c0v[1]), make_float2(d1[0], d1[1]), sp, cp);
+      s2[0] = sp.x;
+      s2[1] = sp.y;
+      c2v[0] = cp.x;
+      c2v[1] = cp.y;
+    }
+    rotate_small(s0[2], c0v[2], d1[2], s2[2], c2v[2]);
     abc_stage_k(a.habc[0], s2, c2v, d2);
     {
       float s3[3], c3[3], dmax = 0.0f;
@@ -460,11 +466,12 @@ __device__ __forceinline__ bool dg_node_safe(const AdvArgs& a, double x, double 
 }
 
 // SAFE: the instantiation for AdvArgs::rot_safe (rk4_step's angle-check-free ABC step).  The
-// compensated float kernels are held to 40 registers, six 256-thread blocks per SM: the few
-// spilled words (outside the step loop) cost less than the warps gained (2D 16.99 -> 16.64 ms,
-// 3D 46.66 -> 45.36 ms against 48 and 47 registers).
+// compensated float kernels are held to five (double gyre, 48 registers) and six (ABC, 40
+// registers) 256-thread blocks per SM: measured on the full meshes, the double gyre with its
+// paired stage-four rotation runs 15.84 ms at 40 registers and 15.53 ms at 48, the ABC flow
+// (before its pairing) 45.4 ms at 40 and 46.7 ms at 47 (the few words spilled at 40 sit outside the step loop).
 template <int KIND, int DIM, int PREC, int OUT, typename CT, bool SAFE = false>
-__global__ void __launch_bounds__(256, PREC == P32C ? 6 : 1) k_advect(AdvArgs a) {
+__global__ void __launch_bounds__(256, PREC == P32C ? (KIND == FTLE_FLOW_DOUBLE_GYRE ? 5 : 6) : 1) k_advect(AdvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kTable = (KIND == FTLE_FLOW_DOUBLE_GYRE);
   float2* tab32 = reinterpret_cast<float2*>(smem_raw);

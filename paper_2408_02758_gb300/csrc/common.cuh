@@ -88,6 +88,18 @@ __device__ __forceinline__ void fsincospi(float x, float& s, float& c) {
   quarter_turn(t, ps, pc, s, c);
 }
 
+// ------------------------------------------------------------------ paired float arithmetic
+// sm_100 and later issue two float lanes in one instruction (fma/mul/add .f32x2), each lane
+// rounded exactly as the scalar instruction.  The FP32 pipe's rate stays the same, but a paired
+// instruction takes one issue slot for two results, which frees slots for the integer and
+// conversion work beside an FMA-bound loop.  The paired helpers below give the bits of their
+// scalar counterparts lane by lane.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
 // pi/2 in three parts: A (8 significant bits) and B (13) make k*A and k*B exact for |k| < 2^11;
 // C is the rest, rounded.
 constexpr float kPio2A = 0x1.92p+0f;
@@ -271,6 +283,15 @@ __device__ __forceinline__ void rotate_small(float s0, float c0, float th, float
   const float cm = t2 * fmaf(t2, 1.0f / 24.0f, -0.5f);
   s = fmaf(s0, cm, fmaf(c0, st, s0));
   c = fmaf(c0, cm, fmaf(-s0, st, c0));
+}
+
+// rotate_small of both lanes.
+__device__ __forceinline__ void rotate_small2(float2 s0, float2 c0, float2 th, float2& s, float2& c) {
+  const float2 t2 = mul2(th, th);
+  const float2 st = fma2(mul2(th, t2), f2(-1.0f / 6.0f), th);
+  const float2 cm = mul2(t2, fma2(t2, f2(1.0f / 24.0f), f2(-0.5f)));
+  s = fma2(s0, cm, fma2(c0, st, s0));
+  c = fma2(c0, cm, fma2(neg2(s0), st, c0));
 }
 
 // --- double gyre, double precision

@@ -41,9 +41,13 @@ def test_batch_equals_single_instances(batch, kappa):
     for w, dm, o in zip(ws_list, meshes, outs):
         single, cnt = _single(ftle, w, dm, opt)
         got = o.double().cpu().numpy()
-        # identical arithmetic except the float-float time coefficients of re-advected nodes
-        same = got == single
-        assert np.all(same | (np.abs(got - single) <= 1e-9 * np.abs(single))), w.name
+        # identical arithmetic except the time coefficients of re-advected nodes: the batched
+        # re-advection turns (sin, cos)(omega t) per half step where the single one reads a table
+        # of double sines, so those nodes agree to float-float accuracy, which can move the float
+        # output by one rounding; every other node is bit-identical
+        diff = got != single
+        assert np.count_nonzero(diff) <= cnt["n_readvected"], w.name
+        assert np.all(np.abs(got - single)[diff] <= 2.0**-23 * np.abs(single)[diff]), w.name
         n_refined += cnt["n_readvected"]
     if kappa > 0:
         assert n_refined > 0  # the refinement path ran
