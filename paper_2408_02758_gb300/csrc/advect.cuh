@@ -466,12 +466,11 @@ __device__ __forceinline__ bool dg_node_safe(const AdvArgs& a, double x, double 
 }
 
 // SAFE: the instantiation for AdvArgs::rot_safe (rk4_step's angle-check-free ABC step).  The
-// compensated float kernels are held to five (double gyre, 48 registers) and six (ABC, 40
-// registers) 256-thread blocks per SM: measured on the full meshes, the double gyre with its
-// paired stage-four rotation runs 15.84 ms at 40 registers and 15.53 ms at 48, the ABC flow
-// (before its pairing) 45.4 ms at 40 and 46.7 ms at 47 (the few words spilled at 40 sit outside the step loop).
+// compensated float kernels are held to five 256-thread blocks per SM (48 registers): measured
+// on the full meshes with the paired rotations, the double gyre runs 15.84 ms at 40 registers
+// (six blocks), 15.47 at 48 and 15.83 at 64 (four); the ABC flow 44.84 ms at 40 and 44.11 at 47.
 template <int KIND, int DIM, int PREC, int OUT, typename CT, bool SAFE = false>
-__global__ void __launch_bounds__(256, PREC == P32C ? (KIND == FTLE_FLOW_DOUBLE_GYRE ? 5 : 6) : 1) k_advect(AdvArgs a) {
+__global__ void __launch_bounds__(256, PREC == P32C ? 5 : 1) k_advect(AdvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kTable = (KIND == FTLE_FLOW_DOUBLE_GYRE);
   float2* tab32 = reinterpret_cast<float2*>(smem_raw);
