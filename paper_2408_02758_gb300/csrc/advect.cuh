@@ -264,8 +264,15 @@ __device__ __forceinline__ void abc_stage_rot(const float* co, const float* d, c
                                               float& mx, float* k) {
   float s[3], c[3];
   if constexpr (CHECK) mx = fmaxf(mx, fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))));
-#pragma unroll
-  for (int q = 0; q < 3; ++q) rotate_small(s0[q], c0[q], d[q], s[q], c[q]);
+  {  // x and y in one paired rotation, z alone
+    float2 sp, cp;
+    rotate_small2(make_float2(s0[0], s0[1]), make_float2(c0[0], c0[1]), make_float2(d[0], d[1]), sp, cp);
+    s[0] = sp.x;
+    s[1] = sp.y;
+    c[0] = cp.x;
+    c[1] = cp.y;
+  }
+  rotate_small(s0[2], c0[2], d[2], s[2], c[2]);
   abc_stage_k(co, s, c, k);
 }
 
@@ -468,7 +475,8 @@ __device__ __forceinline__ bool dg_node_safe(const AdvArgs& a, double x, double 
 // SAFE: the instantiation for AdvArgs::rot_safe (rk4_step's angle-check-free ABC step).  The
 // compensated float kernels are held to five 256-thread blocks per SM (48 registers): measured
 // on the full meshes with the paired rotations, the double gyre runs 15.84 ms at 40 registers
-// (six blocks), 15.47 at 48 and 15.83 at 64 (four); the ABC flow 44.84 ms at 40 and 44.11 at 47.
+// (six blocks), 15.47 at 48 and 15.83 at 64 (four); the ABC flow (stage-two pairing alone)
+// 44.84 ms at 40 and 44.11 at 47.
 template <int KIND, int DIM, int PREC, int OUT, typename CT, bool SAFE = false>
 __global__ void __launch_bounds__(256, PREC == P32C ? 5 : 1) k_advect(AdvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
