@@ -256,6 +256,19 @@ __device__ __forceinline__ void abc_stage_k(const float* co, const float* s, con
   k[2] = fmaf(co[2], s[1], co[1] * c[0]);
 }
 
+// rotate_small of the (sin, cos) pairs of x, y and z by the angles d: x and y as one paired
+// rotation, z alone.
+__device__ __forceinline__ void rotate_small_xyz(const float* s0, const float* c0, const float* d, float* s,
+                                                 float* c) {
+  float2 sp, cp;
+  rotate_small2(make_float2(s0[0], s0[1]), make_float2(c0[0], c0[1]), make_float2(d[0], d[1]), sp, cp);
+  s[0] = sp.x;
+  s[1] = sp.y;
+  c[0] = cp.x;
+  c[1] = cp.y;
+  rotate_small(s0[2], c0[2], d[2], s[2], c[2]);
+}
+
 // ABC stage two, three or four of the compensated step: stage one's (sin, cos) of x, y, z rotated
 // by the stage increments d (radians); with CHECK the largest increment joins `mx`.  co = (A, B, C) times
 // the scale of the value returned (the next stage's increment, or h/6 k4).
@@ -264,15 +277,7 @@ __device__ __forceinline__ void abc_stage_rot(const float* co, const float* d, c
                                               float& mx, float* k) {
   float s[3], c[3];
   if constexpr (CHECK) mx = fmaxf(mx, fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))));
-  {  // x and y in one paired rotation, z alone
-    float2 sp, cp;
-    rotate_small2(make_float2(s0[0], s0[1]), make_float2(c0[0], c0[1]), make_float2(d[0], d[1]), sp, cp);
-    s[0] = sp.x;
-    s[1] = sp.y;
-    c[0] = cp.x;
-    c[1] = cp.y;
-  }
-  rotate_small(s0[2], c0[2], d[2], s[2], c[2]);
+  rotate_small_xyz(s0, c0, d, s, c);
   abc_stage_k(co, s, c, k);
 }
 
@@ -393,15 +398,7 @@ __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const
     // the dropped (d2 - d1)^2 / 2 stays near float rounding: kTinyMax); stage four turns stage
     // one's by d3
     float s2[3], c2v[3];
-    {  // x and y in one paired rotation, z alone
-      float2 sp, cp;
-      rotate_small2(make_float2(s0[0], s0[1]), make_float2(c0v[0], c0v[1]), make_float2(d1[0], d1[1]), sp, cp);
-      s2[0] = sp.x;
-      s2[1] = sp.y;
-      c2v[0] = cp.x;
-      c2v[1] = cp.y;
-    }
-    rotate_small(s0[2], c0v[2], d1[2], s2[2], c2v[2]);
+    rotate_small_xyz(s0, c0v, d1, s2, c2v);
     abc_stage_k(a.habc[0], s2, c2v, d2);
     {
       float s3[3], c3[3], dmax = 0.0f;
