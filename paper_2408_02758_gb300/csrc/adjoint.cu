@@ -150,10 +150,9 @@ __device__ __forceinline__ DgDer dg_derivs32_rot(float piA, float as, float e1, 
   const float w = fmaf(as, e1 + dx, 1.0f);
   const float tf = kPiF * fmaf(dx, w, dg), ty = kPiF * dy;
   mx = fmaxf(mx, fmaxf(fabsf(tf), fabsf(ty)));
-  float sf, cf, sy, cy;
-  rotate_small(sf0, cf0, tf, sf, cf);
-  rotate_small(sy0, cy0, ty, sy, cy);
-  return dg_derivs_sc(piA, as, fmaf(as, dx, w), xs, sf, cf, sy, cy);
+  float2 s, c;  // lanes: pi f, pi y
+  rotate_small2(make_float2(sf0, sy0), make_float2(cf0, cy0), make_float2(tf, ty), s, c);
+  return dg_derivs_sc(piA, as, fmaf(as, dx, w), xs, s.x, c.x, s.y, c.y);
 }
 
 // Segment table per half step: (a, b_l) of the forward kernel, sin(omega t), t cos(omega t).
@@ -258,28 +257,29 @@ __global__ void __launch_bounds__(kAdjBlock) k_adjoint_rk4(AdvArgs a, const floa
           d3 = dg_derivs32(piA, t1.x, b1, z3x, z3y);
           d4 = dg_derivs32(piA, t2.x, b2, fmaf(h, d3.u0, xk.x), fmaf(h, d3.u1, xk.y));
         }
-        float kb1x = h6 * lam0, kb1y = h6 * lam1, kb2x = h3 * lam0, kb2y = h3 * lam1;
-        float kb3x = h3 * lam0, kb3y = h3 * lam1;
-        const float kb4x = h6 * lam0, kb4y = h6 * lam1;
-        float xbx = lam0, xby = lam1;
-        auto stage = [&](const DgDer& d, float kbx, float kby, const float4& tc, float& ybx, float& yby) {
-          ybx = fmaf(-d.j11, kbx, d.j10 * kby);
-          yby = fmaf(d.j01, kbx, d.j11 * kby);
-          const float qk = fmaf(d.q0, kbx, d.q1 * kby);
-          s0 = fmaf(d.pA0, kbx, fmaf(d.pA1, kby, s0));
+        // the stage adjoints kb, the accumulated xb and lambda carry (x, y) as paired lanes
+        const float2 lam = make_float2(lam0, lam1);
+        float2 kb1 = mul2(f2(h6), lam), kb2 = mul2(f2(h3), lam), kb3 = kb2;
+        const float2 kb4 = kb1;
+        float2 xb = lam;
+        auto stage = [&](const DgDer& d, float2 kb, const float4& tc) -> float2 {
+          const float2 yb = make_float2(fmaf(-d.j11, kb.x, d.j10 * kb.y), fmaf(d.j01, kb.x, d.j11 * kb.y));
+          const float qk = fmaf(d.q0, kb.x, d.q1 * kb.y);
+          s0 = fmaf(d.pA0, kb.x, fmaf(d.pA1, kb.y, s0));
           s1 = fmaf(tc.z, qk, s1);
           s2 = fmaf(eps * tc.w, qk, s2);
+          return yb;
         };
-        float ybx, yby;
-        stage(d4, kb4x, kb4y, t2, ybx, yby);
-        xbx += ybx; xby += yby; kb3x = fmaf(h, ybx, kb3x); kb3y = fmaf(h, yby, kb3y);
-        stage(d3, kb3x, kb3y, t1, ybx, yby);
-        xbx += ybx; xby += yby; kb2x = fmaf(h2, ybx, kb2x); kb2y = fmaf(h2, yby, kb2y);
-        stage(d2, kb2x, kb2y, t1, ybx, yby);
-        xbx += ybx; xby += yby; kb1x = fmaf(h2, ybx, kb1x); kb1y = fmaf(h2, yby, kb1y);
-        stage(d1, kb1x, kb1y, t0, ybx, yby);
-        lam0 = xbx + ybx;
-        lam1 = xby + yby;
+        float2 yb = stage(d4, kb4, t2);
+        xb = add2(xb, yb); kb3 = fma2(f2(h), yb, kb3);
+        yb = stage(d3, kb3, t1);
+        xb = add2(xb, yb); kb2 = fma2(f2(h2), yb, kb2);
+        yb = stage(d2, kb2, t1);
+        xb = add2(xb, yb); kb1 = fma2(f2(h2), yb, kb1);
+        yb = stage(d1, kb1, t0);
+        const float2 ln = add2(xb, yb);
+        lam0 = ln.x;
+        lam1 = ln.y;
       }
       th0 += kPi * (double)s0;  // the pA terms are du/dA / pi
       th1 += (double)s1;

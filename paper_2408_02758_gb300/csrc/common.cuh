@@ -89,7 +89,7 @@ __device__ __forceinline__ void fsincospi(float x, float& s, float& c) {
 }
 
 // ------------------------------------------------------------------ paired float arithmetic
-// sm_100 and later issue two float lanes in one instruction (fma/mul .f32x2), each lane
+// sm_100 and later issue two float lanes in one instruction (fma/mul/add .f32x2), each lane
 // rounded exactly as the scalar instruction.  The FP32 pipe's rate stays the same, but a paired
 // instruction takes one issue slot for two results, which frees slots for the integer and
 // conversion work beside an FMA-bound loop.  The paired helpers below give the bits of their
@@ -97,6 +97,7 @@ __device__ __forceinline__ void fsincospi(float x, float& s, float& c) {
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 // pi/2 in three parts: A (8 significant bits) and B (13) make k*A and k*B exact for |k| < 2^11;
