@@ -220,8 +220,8 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
     // stage three turns stage two's pairs by the angle differences to first order: with the
     // half-step increment D2 = D / 2 and the stage-two angle bound S2 (pi f and pi y together),
     // |d pi f| <= pi D2 S2 (1 + |eps| (2 + 2 D2)) (dg cancels, k_u moves by at most the angles)
-    // and |d pi y| <= pi D2 pi ((1 + 2 |eps| (1 + D2)) S2 + |eps| |omega| |h| + 2 |eps| D2)
-    // (k_v adds the slope's change), each to stay within kTinyMax
+    // and |d pi y| <= pi D2 ((1 + 2 |eps| (1 + D2)) S2 + |eps| |omega| |h| + 2 |eps| D2) (the
+    // y angle's scale is pi D2; k_v adds the slope's change), each to stay within kTinyMax
     const double D2 = 0.5 * D;
     const double S2 = kPi * (D2 * (1.0 + eps * (2.0 + D2)) + 0.5 * eps * om * h) +
                       kPi * D2 * (1.0 + 2.0 * eps * (1.0 + D2));
