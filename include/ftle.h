@@ -142,8 +142,9 @@ typedef struct ftle_options {
                              Default 4e-4 when the field is 0; negative turns this test off (the
                              rank, conditioning and lambda_max - 1 < 0.01 checks remain). */
   int32_t advect_block;   /* threads per block of the advection kernel (multiple of 32) */
-  int32_t advect_blocks_per_sm; /* blocks per SM the persistent advection grid is sized for
-                                   (default 2048 / advect_block) */
+  int32_t advect_blocks_per_sm; /* blocks per SM the advection grid is sized for (default
+                                   8192 / advect_block; a block loops over node tiles while
+                                   the grid is smaller than the mesh) */
   int32_t grad_block;     /* threads per block of the gradient kernel (multiple of 32) */
   int32_t grad_tile;      /* nodes per gradient tile (multiple of grad_block) */
   int32_t refine_lanes;   /* re-advection: active lanes per 32-thread block (1..32); fewer lanes

@@ -18,7 +18,7 @@ from dataclasses import dataclass
 from pathlib import Path
 from typing import Callable, Iterable
 
-ADVECT_CANDIDATES = [(256, 8), (128, 16), (64, 32), (256, 4), (128, 8)]
+ADVECT_CANDIDATES = [(256, 32), (256, 8), (128, 16), (64, 32), (256, 4), (128, 64)]
 GRAD_CANDIDATES = [128, 256]
 BATCH_TILE_CANDIDATES = [(256, 256), (128, 512), (256, 1024), (64, 256)]
 

@@ -373,7 +373,10 @@ int run_advect(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
   const int out = precision == FTLE_PREC_FP64 ? O64 : (precision == FTLE_PREC_FP32 ? O32 : O32PAIR);
   int block = L.advect_block;
   if (prec == P64 && block > 128) block = 128;
-  const int grid = grid_for(m->n_nodes, block, L.advect_bps > 0 ? L.advect_bps : 2048 / block);
+  // by default a grid of 8192 / block blocks per SM (32 of 256 threads), more than fit at once:
+  // blocks of few node tiles even out the end of the launch (measured against 8 per SM: 2D
+  // 15.47 -> 15.34 ms, 3D 43.59 -> 43.43 ms)
+  const int grid = grid_for(m->n_nodes, block, L.advect_bps > 0 ? L.advect_bps : 8192 / block);
   return launch_advect(fl->kind, m->dim, prec, out, m->coord_fp64 != 0, a, grid, block, s);
 }
 
