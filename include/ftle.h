@@ -192,6 +192,29 @@ int ftle_advect(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double 
                 int32_t precision, void* flowmap, void* checkpoints, int32_t ckpt_every,
                 const ftle_options* opt, void* stream);
 
+/* The bounds behind ftle_advect's unchecked steps (FTLE_PREC_FP32C, double gyre and ABC flow).
+ * The compensated step evaluates stage one's sines and cosines and turns them for stages two to
+ * four by the small stage angles (Taylor to third order), stage three from stage two's by the
+ * angle differences to first order.  When the host bounds every angle and difference of a step
+ * of size |dt| within the turns' limits, the kernels drop the per-step angle check (double gyre:
+ * for nodes starting in its invariant domain [0, 2] x [0, 1]; ABC: everywhere):
+ *   angle_bound  bound on every stage angle, radians (double gyre: the larger of pi f's and pi y's);
+ *   diff_bound   bound on stage three's angle differences;
+ *   angle_limit, diff_limit  the limits with their 1e-3 margin (0.05 and 3e-4 before it);
+ *   unchecked    1 when both bounds are within their limits, else 0.
+ * Flows without the rotated step (linear, saddle): unchecked = 0, both bounds +inf.
+ * Host only (no device work).  Errors: FTLE_EINVAL (null flow or out, unknown kind, parameters
+ * or dt not finite, dt = 0). */
+typedef struct {
+  int32_t unchecked;
+  int32_t reserved;
+  double angle_bound;
+  double diff_bound;
+  double angle_limit;
+  double diff_limit;
+} ftle_rotation_info;
+int ftle_rotation_bounds(const ftle_flow* flow, double dt, ftle_rotation_info* out);
+
 /* The FTLE core (Section 2.1, Table 1) over the CSR neighbour lists (Section 2.2).
  *   flowmap     device in (as written by ftle_advect for the same precision).
  *   ftle_out    device out [n_nodes]: float, or double for FTLE_PREC_FP64.  NaN where the

@@ -186,6 +186,54 @@ int launch_advect(int kind, int dim, int prec, int out, bool coord64, const AdvA
   return launch_advect_misc(kind, dim, prec, out, coord64, args, grid, block, smem, stream);
 }
 
+// Bounds on the stage angles of one RK4 step of size |h| (radians) and on stage three's angle
+// differences, for the flows whose compensated step turns stage one's sines and cosines
+// (rk4_step); returns false for the others.
+//   Double gyre, nodes in [0, 2] x [0, 1] (the invariant domain their trajectories keep): the x
+//   increment of a full step is at most D = |h| pi |A|, so pi f moves by at most
+//   pi (D (1 + |eps| (2 + D)) + |eps| |omega| |h|) and pi y by at most
+//   pi |h| pi |A| (1 + 2 |eps| (1 + D)).  Stage three turns stage two's pairs by the angle
+//   differences to first order: with the half-step increment D2 = D / 2 and the stage-two angle
+//   bound S2 (pi f and pi y together), |d pi f| <= pi D2 S2 (1 + |eps| (2 + 2 D2)) (dg cancels,
+//   k_u moves by at most the angles) and |d pi y| <= pi D2 ((1 + 2 |eps| (1 + D2)) S2 +
+//   |eps| |omega| |h| + 2 |eps| D2) (the y angle's scale is pi D2; k_v adds the slope's change).
+//   ABC: a stage increment of component q is a step fraction <= |h| times P_q sin + Q_q cos, with
+//   (P, Q) = (A, C), (B, A), (C, B), so at most |h| U with U the largest pair sum; stage three's
+//   turn from stage two, d2 - d1 = h/2 (k2 - k1), is at most h^2/4 L U with the flow's Lipschitz
+//   constant L (max-norm row sums), this same maximum pair sum for the ABC flow.
+static bool rotation_bounds(const ftle_flow* f, double h_signed, double* angle, double* diff) {
+  const double h = fabs(h_signed);
+  if (f->kind == FTLE_FLOW_DOUBLE_GYRE) {
+    const double A = fabs(f->p[0]), eps = fabs(f->p[1]), om = fabs(f->p[2]);
+    const double D = h * kPi * A;
+    const double tf = kPi * (D * (1.0 + eps * (2.0 + D)) + eps * om * h);
+    const double ty = kPi * h * kPi * A * (1.0 + 2.0 * eps * (1.0 + D));
+    const double D2 = 0.5 * D;
+    const double S2 = kPi * (D2 * (1.0 + eps * (2.0 + D2)) + 0.5 * eps * om * h) +
+                      kPi * D2 * (1.0 + 2.0 * eps * (1.0 + D2));
+    const double df = kPi * D2 * S2 * (1.0 + eps * (2.0 + 2.0 * D2));
+    const double dy = kPi * D2 * ((1.0 + 2.0 * eps * (1.0 + D2)) * S2 + eps * om * h + 2.0 * eps * D2);
+    *angle = fmax(tf, ty);
+    *diff = fmax(df, dy);
+    return true;
+  }
+  if (f->kind == FTLE_FLOW_ABC) {
+    const double A = fabs(f->p[0]), B = fabs(f->p[1]), C = fabs(f->p[2]);
+    const double U = fmax(A + C, fmax(B + A, C + B));
+    *angle = h * U;
+    *diff = 0.25 * h * h * U * U;
+    return true;
+  }
+  *angle = *diff = INFINITY;
+  return false;
+}
+
+// The unchecked steps apply when both bounds sit within the turns' limits; the 1e-3 margin covers
+// the float rounding of the angles and of positions a rounding off the walls.
+static bool rotation_unchecked(double angle, double diff) {
+  return angle <= (double)kRotMax * (1.0 - 1e-3) && diff <= (double)kTinyMax * (1.0 - 1e-3);
+}
+
 AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double T, double dt, int nsteps) {
   AdvArgs a;
   memset(&a, 0, sizeof a);
@@ -209,41 +257,12 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
   if (f->kind == FTLE_FLOW_DOUBLE_GYRE) {
     a.hs_pi[0] = (float)(kPi * 0.5 * a.h * kPi * f->p[0]);
     a.hs_pi[1] = (float)(kPi * a.h * kPi * f->p[0]);
-    // stage angles of a node in [0, 2] x [0, 1] (the invariant domain its trajectory keeps): the
-    // x increment is at most D = |h| pi |A|, so pi f moves by at most pi (D (1 + |eps| (2 + D)) +
-    // |eps| |omega| |h|) and pi y by at most pi |h| pi |A| (1 + 2 |eps| (1 + D)); a margin covers
-    // the float rounding of the angles and of positions a rounding off the walls
-    const double A = fabs(f->p[0]), eps = fabs(f->p[1]), om = fabs(f->p[2]), h = fabs(a.h);
-    const double D = h * kPi * A;
-    const double tf = kPi * (D * (1.0 + eps * (2.0 + D)) + eps * om * h);
-    const double ty = kPi * h * kPi * A * (1.0 + 2.0 * eps * (1.0 + D));
-    // stage three turns stage two's pairs by the angle differences to first order: with the
-    // half-step increment D2 = D / 2 and the stage-two angle bound S2 (pi f and pi y together),
-    // |d pi f| <= pi D2 S2 (1 + |eps| (2 + 2 D2)) (dg cancels, k_u moves by at most the angles)
-    // and |d pi y| <= pi D2 ((1 + 2 |eps| (1 + D2)) S2 + |eps| |omega| |h| + 2 |eps| D2) (the
-    // y angle's scale is pi D2; k_v adds the slope's change), each to stay within kTinyMax
-    const double D2 = 0.5 * D;
-    const double S2 = kPi * (D2 * (1.0 + eps * (2.0 + D2)) + 0.5 * eps * om * h) +
-                      kPi * D2 * (1.0 + 2.0 * eps * (1.0 + D2));
-    const double df = kPi * D2 * S2 * (1.0 + eps * (2.0 + 2.0 * D2));
-    const double dy = kPi * D2 * ((1.0 + 2.0 * eps * (1.0 + D2)) * S2 + eps * om * h + 2.0 * eps * D2);
-    a.rot_safe = (fmax(tf, ty) <= (double)kRotMax * (1.0 - 1e-3) &&
-                  fmax(df, dy) <= (double)kTinyMax * (1.0 - 1e-3)) ? 1 : 0;
   }
   const double hsc[3] = {0.5 * a.h, a.h, a.h / 6.0};
   for (int s = 0; s < 3; ++s)
     for (int q = 0; q < 3; ++q) a.habc[s][q] = (float)(hsc[s] * f->p[q]);
-  if (f->kind == FTLE_FLOW_ABC) {
-    // a stage increment of component q is a step fraction <= |h| times P_q sin + Q_q cos, with
-    // (P, Q) = (A, C), (B, A), (C, B); a margin covers the float rounding of the increments
-    // and stage three's turn from stage two, d2 - d1 = h/2 (k2 - k1), is at most h^2/4 L U with
-    // the flow's speed bound U and Lipschitz constant L (max-norm row sums), both this same
-    // maximum pair sum for the ABC flow
-    const double A = fabs(f->p[0]), B = fabs(f->p[1]), C = fabs(f->p[2]);
-    const double U = fmax(A + C, fmax(B + A, C + B));
-    const double bound = fabs(a.h) * U, tiny = 0.25 * a.h * a.h * U * U;
-    a.rot_safe = (bound <= (double)kRotMax * (1.0 - 1e-3) && tiny <= (double)kTinyMax * (1.0 - 1e-3)) ? 1 : 0;
-  }
+  double angle, diff;
+  if (rotation_bounds(f, a.h, &angle, &diff)) a.rot_safe = rotation_unchecked(angle, diff) ? 1 : 0;
   return a;
 }
 
@@ -441,6 +460,22 @@ int ftle_advect(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double 
   if ((rc = check_launch(L))) return rc;
   return run_advect(mesh, flow, t0, T, dt, nsteps, precision, flowmap, checkpoints, ckpt_every, L,
                     (cudaStream_t)stream);
+}
+
+int ftle_rotation_bounds(const ftle_flow* flow, double dt, ftle_rotation_info* out) {
+  int rc;
+  if ((rc = check_flow(flow, flow && flow->kind == FTLE_FLOW_ABC ? 3 : 2))) return rc;
+  if (!out) return fail(FTLE_EINVAL, "out is NULL");
+  if (!isfinite(dt) || dt == 0.0) return fail(FTLE_EINVAL, "dt must be finite and non-zero");
+  double angle, diff;
+  const bool rotated = rotation_bounds(flow, dt, &angle, &diff);
+  out->unchecked = rotated && rotation_unchecked(angle, diff) ? 1 : 0;
+  out->reserved = 0;
+  out->angle_bound = angle;
+  out->diff_bound = diff;
+  out->angle_limit = (double)kRotMax * (1.0 - 1e-3);
+  out->diff_limit = (double)kTinyMax * (1.0 - 1e-3);
+  return FTLE_OK;
 }
 
 int ftle_gradient_eig(const ftle_mesh* mesh, const void* flowmap, int32_t precision, double T,

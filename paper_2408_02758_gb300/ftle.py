@@ -40,6 +40,11 @@ class ftle_counters(Structure):
                 ("reserved", c_uint64 * 5)]
 
 
+class ftle_rotation_info(Structure):
+    _fields_ = [("unchecked", c_int32), ("reserved", c_int32), ("angle_bound", c_double), ("diff_bound", c_double),
+                ("angle_limit", c_double), ("diff_limit", c_double)]
+
+
 class ftle_options(Structure):
     _fields_ = [("refine_kappa", c_double), ("advect_block", c_int32), ("advect_blocks_per_sm", c_int32),
                 ("grad_block", c_int32), ("grad_tile", c_int32), ("refine_lanes", c_int32),
@@ -59,6 +64,7 @@ _SIGS = [
     ("ftle_version", c_int, []),
     ("ftle_last_error", c_char_p, []),
     ("ftle_status_string", c_char_p, [c_int]),
+    ("ftle_rotation_bounds", c_int, [POINTER(ftle_flow), c_double, POINTER(ftle_rotation_info)]),
     ("ftle_flowmap_bytes", c_size_t, [c_int32, c_int64, c_int32]),
     ("ftle_checkpoint_bytes", c_size_t, [c_int32, c_int64, c_int32]),
     ("ftle_workspace_bytes", c_size_t, [c_int64]),
@@ -245,6 +251,15 @@ class DeviceMesh:
 
 def ftle_version() -> int:
     return int(lib().ftle_version())
+
+
+def ftle_rotation_bounds(flow, dt: float) -> dict:
+    """Host-side bounds behind the advection's unchecked rotated steps (no device work)."""
+    f = make_flow(flow)
+    info = ftle_rotation_info()
+    _check("ftle_rotation_bounds", lib().ftle_rotation_bounds(ctypes.byref(f), dt, ctypes.byref(info)))
+    return {"unchecked": bool(info.unchecked), "angle_bound": info.angle_bound, "diff_bound": info.diff_bound,
+            "angle_limit": info.angle_limit, "diff_limit": info.diff_limit}
 
 
 def ftle_flowmap_bytes(dim: int, n_nodes: int, precision) -> int:
