@@ -3,11 +3,14 @@
 least-squares gradient / Cauchy-Green / lambda_max / FTLE, FP64 refinement of float-sensitive
 nodes) over a synthetic workload, inputs resident in HBM.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 1] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 2] [--impl ours|reference]
 
-Default workload: 2048 x 1024 jittered triangle mesh (2,097,152 nodes, 6-neighbour CSR) over
-[0,2] x [0,1], double gyre A=0.1 eps=0.25 omega=2pi/10, RK4 dt=0.01 over T=15 (1500 steps),
-compensated-float advection with the FP64 path for float-sensitive nodes.
+Default workload: 256^3 jittered Kuhn tetrahedral mesh (16,777,216 nodes, 14-neighbour lists)
+over [0,2pi]^3, ABC flow A=sqrt(3) B=sqrt(2) C=1, RK4 dt=0.01 over T=5 (500 steps),
+compensated-float advection with the FP64 path for float-sensitive nodes; the gradient reads the
+paper's fixed-width -1-padded neighbour list.  --workload 1 is the 2048 x 1024 jittered
+triangle mesh with the double gyre (T = 15), 3 the 64-instance batch, 4 the differentiable one.
+Launch shapes come from the autotuner (tuned outside the timed region).
 
 Each step's kernels are bracketed by CUDA events on the launching stream; L2 is flushed by a
 320 MiB write between steps, outside the events.  Prints one JSON line (rank 0).
@@ -114,6 +117,39 @@ def dist_setup():
     return r.world, r.rank, r.local
 
 
+# ----------------------------------------------------------------------------- workload description
+
+L2_NOTE = "flushed between steps (320 MiB write, outside the events)"
+
+
+def layout_of(args) -> str:
+    return "stencil" if args.stencil else ("csr" if args.csr else "ell")
+
+
+def workload_config(w, world: int, layout: str) -> dict:
+    """The `config` of a single-problem line; both arms print the same one."""
+    import numpy as np
+
+    width = int(np.diff(w.mesh.row_ptr).max()) if w.mesh.n_nodes else 0
+    return {"workload": w.name, "nodes": w.mesh.n_nodes, "nnz": w.mesh.nnz, "steps_rk4": w.n_steps, "T": w.T,
+            "dt": w.dt, "precision": w.precision, "l2": L2_NOTE,
+            "neighbours": {"stencil": "implicit lattice stencil", "csr": "CSR rows",
+                           "ell": f"fixed-width list, width {width} (-1 padded)"}[layout],
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+def batched_config(wl_all, world: int) -> dict:
+    return {"workload": "dg2d_batched_64", "instances": len(wl_all), "nodes": sum(w.mesh.n_nodes for w in wl_all),
+            "node_steps": sum(w.mesh.n_nodes * w.n_steps for w in wl_all), "precision": "fp32c",
+            "parallelism": f"instances split longest-first over {world} GPUs" if world > 1 else "single GPU",
+            "l2": "flushed between steps", "execution": "one CUDA graph (persistent LPT queues)"}
+
+
+def differentiable_config(w) -> dict:
+    return {"workload": w.name, "nodes": w.mesh.n_nodes, "steps_rk4": w.n_steps, "ckpt_every": w.extra["ckpt_every"],
+            "precision": "fp32c", "loss": "mean FTLE over nodes with x0 in [0.5, 1.5]", "l2": "flushed between steps"}
+
+
 # ----------------------------------------------------------------------------- CPU oracle leg
 
 
@@ -173,10 +209,10 @@ def run_reference(args, w, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "nodes": w.mesh.n_nodes, "steps_rk4": w.n_steps, "precision": "fp64 oracle"},
+        "config": workload_config(w, world, layout_of(args)),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                          "sample": f"{n_per_step} contiguous nodes of {w.name} per step (full path: RK4 + QR "
-                                   f"least squares + Jacobi), one-row halo advected too"},
+                                   f"least squares + Jacobi), their neighbours advected too"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -217,7 +253,7 @@ def run_batched(args, world, rank, local):
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
                           "steps": 1, "warmup": 0, "ms_per_step": 1000 * dt, "higher_is_better": True,
                           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": "dg2d_batched_64", "nodes": total},
+                          "config": batched_config(wl_all, world),
                           "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                                            "sample": f"the 8 cheapest of 64 instances ({done} nodes)"},
                           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -236,7 +272,14 @@ def run_batched(args, world, rank, local):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
-    plan = ftle.BatchPlan(meshes, [w.flow for w in wl], [w.T for w in wl], 0.01, "fp32c", outs, ws, stream=sh)
+    from paper_2408_02758_gb300 import autotune
+
+    # launch shapes from the autotuner, tuned before the timed region (scheduling only: the
+    # per-node arithmetic, hence every result, is the same for every candidate)
+    with torch.cuda.stream(stream):
+        tuned = autotune.params_for_batch(meshes, [w.flow for w in wl], [w.T for w in wl], 0.01, "fp32c")
+    plan = ftle.BatchPlan(meshes, [w.flow for w in wl], [w.T for w in wl], 0.01, "fp32c", outs, ws,
+                          options=ftle.make_options(**tuned), stream=sh)
     K, W = args.steps, args.warmup
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(W + K)]
     dopt = ftle.make_options(defer_fp64=True)  # FP64 pass of the flagged nodes once, after refinement
@@ -280,10 +323,7 @@ def run_batched(args, world, rank, local):
         "metric": METRIC, "value": total / (ms / 1000), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "dg2d_batched_64", "instances": len(wl_all), "nodes": total,
-                   "node_steps": sum(w.mesh.n_nodes * w.n_steps for w in wl_all), "precision": "fp32c",
-                   "parallelism": f"instances split longest-first over {world} GPUs" if world > 1 else "single GPU",
-                   "l2": "flushed between steps", "execution": "one CUDA graph (persistent LPT queues)"},
+        "config": batched_config(wl_all, world), "tuned": tuned,
         "roofline": {"kernel": "whole batched graph (k_batch_advect dominates)", "bound": "alu", "achieved": ach,
                      "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None},
         "single_instance_sum_ms": single_sum, "batched_speedup_vs_single": single_sum / ms / world,
@@ -352,11 +392,55 @@ def run_differentiable(args, world, rank, local):
         "metric": METRIC + " and d(region-mean FTLE)/d(A,eps,omega)", "value": n / (both / 1000), "unit": UNIT,
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": both, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "nodes": n, "steps_rk4": w.n_steps, "ckpt_every": ce, "precision": "fp32c",
-                   "loss": "mean FTLE over nodes with x0 in [0.5, 1.5]", "l2": "flushed between steps"},
+        "config": differentiable_config(w),
         "forward_only_ms": fwd, "forward_plus_backward_ms": both, "backward_over_forward": (both - fwd) / fwd,
         "gradient": grad.cpu().tolist(), "clocks": clk, "gpu_launches": 9 * K, "cpu_baseline": None, "e2e": None,
         "roofline": None}), flush=True)
+
+
+def run_differentiable_reference(args, world, rank, local):
+    """The FP64 oracle as the reference arm of the differentiable workload: its forward-mode
+    derivative of the weighted FTLE sum, each step on a bounded sample of the region's nodes (a
+    contiguous block of rows with their neighbours; the whole path: RK4 with tangents, QR least
+    squares, Jacobi eigenvectors)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle as O
+    from paper_2408_02758_gb300 import inputs as I
+
+    O.build()
+    w = I.preset(4, scale=args.scale)
+    wts = w.extra["weights"].astype(np.float64)
+    region = np.flatnonzero(wts > 0)
+
+    def sample_step(n_rows: int, k: int):
+        start = (k * 7919 * 256) % max(1, len(region) - n_rows)
+        rows = region[start:start + n_rows]
+        sc, srp, sci, m = O.submesh(w.mesh.coords, w.mesh.row_ptr, w.mesh.col_idx, rows)
+        sw = np.zeros(sc.shape[1])
+        sw[:m] = wts[rows]
+        t0 = time.perf_counter()
+        O.param_grad(sc.astype(np.float64), srp, sci, w.flow.params[:3], w.T, w.dt, sw)
+        return time.perf_counter() - t0
+
+    probe = 1024
+    rate = probe / max(sample_step(probe, 0), 1e-3)
+    n_rows = int(max(probe, min(len(region) // 2, rate * 4.0)))
+    for k in range(args.warmup):
+        sample_step(n_rows, k)
+    times = [sample_step(n_rows, args.warmup + k) for k in range(args.steps)]
+    value = n_rows * args.steps / sum(times)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC + " and d(region-mean FTLE)/d(A,eps,omega)", "value": value,
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": differentiable_config(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{n_rows} contiguous region nodes of {w.name} per step (forward-mode "
+                                   f"derivative of their weighted FTLE, neighbours advected too)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -368,7 +452,9 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", type=int, default=1, help="preset index (0..2; 1 is the benchmark workload)")
+    ap.add_argument("--workload", type=int, default=2,
+                    help="preset index: 0 structured 2D, 1 triangle 2D, 2 tet 3D (default), 3 batched, "
+                         "4 differentiable")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--csr", action="store_true",
@@ -377,6 +463,7 @@ def main():
                     help="gradient over the lattice's implicit neighbours (no neighbour index read)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="lattice axes scaled by this factor (smaller cases for profiler captures)")
+    ap.add_argument("--no-tune", action="store_true", help="default launch shapes instead of the autotuner's")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -387,8 +474,8 @@ def main():
     if args.workload == 3:
         run_batched(args, world, rank, local)
         return
-    if args.workload == 4 and args.impl == "ours":
-        run_differentiable(args, world, rank, local)
+    if args.workload == 4:
+        (run_differentiable if args.impl == "ours" else run_differentiable_reference)(args, world, rank, local)
         return
     w = I.preset(args.workload, scale=args.scale)
 
@@ -437,9 +524,17 @@ def main():
     sh = stream.cuda_stream
     K, W = args.steps, args.warmup
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(W + K)]
+    # launch shapes from the autotuner, tuned before the timed region on this problem (scheduling
+    # only: every candidate computes the same per-node arithmetic)
+    tuned = {}
+    if not args.no_tune:
+        from paper_2408_02758_gb300 import autotune
+
+        with torch.cuda.stream(stream):
+            tuned = autotune.params_for_compute(dm, w.flow, w.T, w.dt, prec)
     # the calls ftle_compute makes, timed one by one: the flagged nodes' FP64 pass runs once, after
     # the re-advection (defer_fp64), as inside ftle_compute
-    opt = ftle.make_options(defer_fp64=True)
+    opt = ftle.make_options(defer_fp64=True, **tuned)
 
     def step(k):
         flush.fill_(float(k))
@@ -490,14 +585,15 @@ def main():
         ci = torch.from_numpy(w.mesh.col_idx).pin_memory()
         oh = torch.empty(n, dtype=torch.float64 if prec == "fp64" else torch.float32).pin_memory()
         hws = ftle.workspace_empty(ftle.ftle_host_workspace_bytes(w.mesh.dim, n, w.mesh.nnz, prec), device=dev)
+        hopt = ftle.make_options(**tuned)
         for _ in range(2):
-            ftle.ftle_compute_host(ch, rp, ci, w.flow, 0.0, w.T, w.dt, prec, oh, hws, stream=sh)
+            ftle.ftle_compute_host(ch, rp, ci, w.flow, 0.0, w.T, w.dt, prec, oh, hws, options=hopt, stream=sh)
         te = []
         for _ in range(args.e2e_steps):
             flush.fill_(0.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ftle.ftle_compute_host(ch, rp, ci, w.flow, 0.0, w.T, w.dt, prec, oh, hws, stream=sh)
+            ftle.ftle_compute_host(ch, rp, ci, w.flow, 0.0, w.T, w.dt, prec, oh, hws, options=hopt, stream=sh)
             te.append(time.perf_counter() - t0)
         h2d = ch.numel() * ch.element_size() + rp.numel() * 4 + ci.numel() * 4
         e2e = {"value": n / statistics.mean(te), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -526,11 +622,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": w.name, "nodes": n, "nnz": nnz, "steps_rk4": w.n_steps, "T": w.T, "dt": w.dt,
-                   "precision": prec, "l2": "flushed between steps (320 MiB write, outside the events)",
-                   "neighbours": ("implicit lattice stencil" if args.stencil else "CSR rows" if args.csr
-                                  else f"fixed-width list, width {dm.desc.ell_width} (-1 padded)"),
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": workload_config(w, world, layout_of(args)), "tuned": tuned or "defaults (--no-tune)",
         "roofline": {"kernel": "k_advect (RK4 flowmap)", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {peaks.get('sm_max_mhz', 2070.0)} MHz "

@@ -28,6 +28,8 @@
  *   - Thread-safe for calls on distinct streams with distinct output/workspace buffers.
  *   - Node coordinates are SoA: coords[d * n_nodes + i], d < dim.  Neighbour lists are CSR:
  *     the neighbours of node i are col_idx[row_ptr[i] .. row_ptr[i+1]), int32, 0 <= j < n_nodes.
+ *     Kernels gather through these indices: ftle_validate_mesh checks them (the entry points do
+ *     so themselves with ftle_options.validate_mesh = 1, ftle_compute_host always).
  *   - T < 0 integrates backward in time; |T| enters the FTLE formula.  The RK4 step is
  *     h = sign(T) |dt|, n = round(|T| / |dt|) steps from t0, stages at t_k, t_k + h/2 (twice),
  *     t_k + h with t_k = t0 + k h.
@@ -155,7 +157,13 @@ typedef struct ftle_options {
                              stay NaN until then).  Ignored, and the pass runs, when ftle_refine
                              would not refine (FP32, or refine_kappa < 0).  ftle_compute does
                              this by itself. */
-  int32_t reserved[2];
+  int32_t validate_mesh;  /* 1: ftle_gradient_eig, ftle_compute and ftle_batch (and
+                             ftle_batch_plan_create) first run ftle_validate_mesh on every mesh
+                             they are given and return FTLE_EINVAL, with nothing else launched,
+                             when an index is out of range.  The check synchronises the stream
+                             once per mesh (it reads its counters back), so it is off by default;
+                             ftle_compute_host always runs it. */
+  int32_t reserved;       /* must be 0 */
 } ftle_options;
 
 /* ---------------------------------------------------------------------------------- sizes */
@@ -247,7 +255,9 @@ int ftle_compute(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double
 
 /* End-to-end from HOST buffers: copies coords (float, or double for FP64), row_ptr and col_idx
  * from host memory into `device_ws`, runs ftle_compute, copies the FTLE field back into
- * ftle_host (float, or double for FP64) and synchronises `stream` before returning.
+ * ftle_host (float, or double for FP64) and synchronises `stream` before returning.  The
+ * copied lists always go through ftle_validate_mesh (on a second stream, while the advection
+ * runs): an index out of range returns FTLE_EINVAL before any kernel reads through it.
  * Host buffers should be pinned for full copy bandwidth.  device_ws must hold
  * ftle_host_workspace_bytes(dim, n_nodes, nnz, precision) bytes. */
 size_t ftle_host_workspace_bytes(int32_t dim, int64_t n_nodes, int64_t nnz, int32_t precision);
@@ -280,6 +290,33 @@ int ftle_csr_from_elements(int64_t n_nodes, int64_t n_elem, int32_t verts_per_el
                            int32_t max_row, int32_t* row_ptr, int32_t* col_idx, int64_t nnz_cap,
                            int64_t* nnz_out, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Validation of a mesh's neighbour lists, the contract of the paper's host-side neighbour
+ * precomputation (Section 2.2): the FTLE core gathers coordinates and flowmaps through these
+ * indices, so every one must name a node.  One pass on the device reads row_ptr, col_idx and
+ * (when set) ell_idx and checks, without dereferencing any value it reads:
+ *   row_ptr[0] = 0, row_ptr non-decreasing, row_ptr[n_nodes] = nnz;
+ *   0 <= col_idx[e] < n_nodes for every e < nnz;
+ *   -1 <= ell_idx[t] < n_nodes for every t < ell_width * n_nodes.
+ *   report     nullable HOST out: how many entries of each array are bad and the position of the
+ *              first (-1 when none).
+ *   workspace  device, >= 256 bytes, 256-byte aligned; bytes 128..175 are overwritten (the start
+ *              of a ftle_workspace_bytes workspace serves, its counters stay as they were).
+ * Synchronous: waits for `stream`.  Returns FTLE_EINVAL (message naming the first bad entry)
+ * when any check fails, FTLE_OK otherwise.  The other entry points check sizes and pointers on
+ * the host but trust the index values; they run this pass themselves when
+ * ftle_options.validate_mesh = 1 (ftle_compute_host always does). */
+typedef struct ftle_mesh_report {
+  int64_t bad_row_ptr;    /* rows i with row_ptr[i+1] < row_ptr[i], row_ptr[0] != 0 (row 0) or
+                             row_ptr[n_nodes] != nnz (row n_nodes - 1) */
+  int64_t bad_col_idx;    /* col_idx entries outside [0, n_nodes) */
+  int64_t bad_ell_idx;    /* ell_idx entries outside [-1, n_nodes) */
+  int64_t first_bad_row;  /* lowest such row, -1 if none */
+  int64_t first_bad_col;  /* lowest such col_idx position, -1 if none */
+  int64_t first_bad_ell;  /* lowest such ell_idx position (s * n_nodes + i), -1 if none */
+} ftle_mesh_report;
+int ftle_validate_mesh(const ftle_mesh* mesh, ftle_mesh_report* report, void* workspace,
+                       size_t workspace_bytes, void* stream);
+
 /* Synchronous read of the counters at the start of `workspace` (waits for `stream`). */
 int ftle_read_counters(const void* workspace, ftle_counters* out, void* stream);
 
@@ -293,15 +330,21 @@ int ftle_read_counters(const void* workspace, ftle_counters* out, void* stream);
  *   - Limit: n_nodes <= FTLE_NOALLOC_MAX_NODES; larger meshes return FTLE_ERANGE, nothing launched.
  *   - Memory: the array (FTLE_NOALLOC_MAX_NODES * 4 + 256 bytes, about 4 MiB) is part of the
  *     library's device image, so every GPU that loads libftle.so holds it until the process exits.
- *   - Set-up: the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call before any stream
- *     capture begins on the device.
+ *   - Set-up: a call outside stream capture looks up the array's device address
+ *     (cudaGetSymbolAddress) with the calling device current; a call on a capturing stream reuses
+ *     the address from the last call on that device outside capture.  So make the first call on
+ *     each device before any stream capture begins there (a first call inside a capture returns
+ *     FTLE_EINVAL), and after a cudaDeviceReset make one call outside capture before capturing
+ *     again.
  *   - Sharing: all calls share the one array, and each call clears the counters it needs at its
  *     start (the array keeps the last call's contents otherwise).  Two calls whose work overlaps
  *     on the GPU (for example on two streams) race on the array and corrupt each other's FP64
  *     node list; serialise them.
  *   - Arguments, outputs and errors otherwise as ftle_gradient_eig (flowmap, ftle_out and
- *     lambda_out are caller device buffers; no counters are returned). */
+ *     lambda_out are caller device buffers; no counters are returned), except that the FP64 pass
+ *     of the flagged nodes always runs inside this call: ftle_options.defer_fp64 = 1 returns
+ *     FTLE_EINVAL, and no ftle_refine can follow this call (its flag list lives in the array,
+ *     not in a workspace an ftle_refine could be given). */
 #define FTLE_NOALLOC_MAX_NODES 1048576
 int ftle_gradient_eig_noalloc(const ftle_mesh* mesh, const void* flowmap, int32_t precision, double T,
                               void* ftle_out, double* lambda_out, const ftle_options* opt,

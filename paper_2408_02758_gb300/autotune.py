@@ -108,6 +108,14 @@ def options_for_compute(mesh, flow, T: float, dt: float, precision: str = "fp32c
     """ftle_options with the fastest advection block shape and gradient block for this problem."""
     from . import ftle
 
+    return ftle.make_options(**params_for_compute(mesh, flow, T, dt, precision, cache, retune))
+
+
+def params_for_compute(mesh, flow, T: float, dt: float, precision: str = "fp32c", cache: Cache | None = None,
+                       retune: bool = False) -> dict:
+    """The launch shapes options_for_compute picks, as ftle.make_options keyword arguments."""
+    from . import ftle
+
     cache = cache or Cache()
     n_steps = int(round(abs(T) / dt))
     key = shape_key(_gpu_name(), "compute", mesh.dim, int(flow.kind), precision, mesh.n_nodes, n_steps)
@@ -130,12 +138,20 @@ def options_for_compute(mesh, flow, T: float, dt: float, precision: str = "fp32c
         gr = pick([{"grad_block": b} for b in GRAD_CANDIDATES], t_grad)
         ch = Choice({**adv.params, **gr.params}, adv.ms + gr.ms)
         cache.put(key, ch)
-    return ftle.make_options(**ch.params)
+    return dict(ch.params)
 
 
 def options_for_batch(meshes, flows, T, dt: float, precision: str = "fp32c", cache: Cache | None = None,
                       retune: bool = False):
     """ftle_options (advection block, gradient tile) with the fastest batched launch sequence."""
+    from . import ftle
+
+    return ftle.make_options(**params_for_batch(meshes, flows, T, dt, precision, cache, retune))
+
+
+def params_for_batch(meshes, flows, T, dt: float, precision: str = "fp32c", cache: Cache | None = None,
+                     retune: bool = False) -> dict:
+    """The launch shapes options_for_batch picks, as ftle.make_options keyword arguments."""
     from . import ftle
 
     cache = cache or Cache()
@@ -155,4 +171,4 @@ def options_for_batch(meshes, flows, T, dt: float, precision: str = "fp32c", cac
 
         ch = pick([{"advect_block": b, "grad_tile": t} for b, t in BATCH_TILE_CANDIDATES], t_batch, repeats=1)
         cache.put(key, ch)
-    return ftle.make_options(**{k: v for k, v in ch.params.items() if k in ("advect_block", "grad_tile")})
+    return {k: v for k, v in ch.params.items() if k in ("advect_block", "grad_tile")}

@@ -7,6 +7,7 @@
 // coefficients (lanes of one warp may belong to different instances).  The sequence can be
 // captured once into a CUDA graph (ftle_batch_plan_*) and replayed.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -289,6 +290,7 @@ struct BatchPlanHost {
   int n_inst = 0, dim = 0, kind = 0, precision = 0, max_steps = 0;
   int adv_block = 256, grad_block = 256, grad_tile = 256, adv_grid = 1, grad_grid = 1;
   bool refine = true;
+  bool validate = false;
   char* ws = nullptr;
   BatchLayout L;
   std::vector<BatchInst> insts;
@@ -371,6 +373,22 @@ int plan_batch(int32_t n_inst, const ftle_mesh* meshes, const ftle_flow* flows, 
       P.grad_items.push_back({q, (int32_t)lo, (int32_t)std::min<int64_t>(meshes[q].n_nodes, lo + P.grad_tile), 0});
   if ((int)P.adv_items.size() > P.L.max_items || (int)P.grad_items.size() > P.L.max_items)
     return fail(FTLE_EINVAL, "batch: blocks narrower than 32 nodes are not supported");
+  P.validate = Lc.validate_mesh;
+  return FTLE_OK;
+}
+
+// ftle_options.validate_mesh: every instance's lists checked before anything else runs
+// (synchronises `s` once per instance).
+int validate_batch(const BatchPlanHost& P, const ftle_mesh* meshes, cudaStream_t s) {
+  if (!P.validate) return FTLE_OK;
+  for (int q = 0; q < P.n_inst; ++q) {
+    const int rc = validate_mesh_sync(&meshes[q], P.ws + P.L.header, s, nullptr);
+    if (rc) {
+      char msg[400];
+      snprintf(msg, sizeof msg, "%s", ftle_last_error());
+      return fail(rc, "batch instance %d: %s", q, msg);
+    }
+  }
   return FTLE_OK;
 }
 
@@ -448,6 +466,7 @@ int ftle_batch(int32_t n_inst, const ftle_mesh* meshes, const ftle_flow* flows, 
   int rc = plan_batch(n_inst, meshes, flows, T, dt, precision, ftle_out, workspace, workspace_bytes, opt, P);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = validate_batch(P, meshes, s))) return rc;
   if ((rc = upload_batch(P, s))) return rc;
   // the host vectors are released on return: wait for the uploads (pageable sources)
   FTLE_CUDA_CHECK(cudaStreamSynchronize(s));
@@ -463,6 +482,7 @@ int ftle_batch_plan_create(int32_t n_inst, const ftle_mesh* meshes, const ftle_f
   if (!p) return fail(FTLE_ENOMEM, "host allocation failed");
   int rc = plan_batch(n_inst, meshes, flows, T, dt, precision, ftle_out, workspace, workspace_bytes, opt, p->host);
   cudaStream_t s = (cudaStream_t)stream;
+  if (!rc) rc = validate_batch(p->host, meshes, s);
   if (!rc) rc = upload_batch(p->host, s);
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize(s);

@@ -156,6 +156,7 @@ Launch resolve_launch(const ftle_options* opt) {
     if (opt->grad_block > 0) L.grad_block = opt->grad_block;
     if (opt->refine_lanes > 0) L.refine_lanes = opt->refine_lanes;
     L.defer_fp64 = opt->defer_fp64 != 0;
+    L.validate_mesh = opt->validate_mesh != 0;
   }
   return L;
 }
@@ -489,6 +490,7 @@ int ftle_gradient_eig(const ftle_mesh* mesh, const void* flowmap, int32_t precis
   const Launch L = resolve_launch(opt);
   if ((rc = check_launch(L))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if (L.validate_mesh && (rc = validate_mesh_sync(mesh, workspace, s, nullptr))) return rc;
   FTLE_CUDA_CHECK(cudaMemsetAsync(workspace, 0, sizeof(ftle_counters), s));
   return run_gradient(mesh, flowmap, precision, T, ftle_out, lambda_out, workspace, L, s,
                       !(L.defer_fp64 && refine_runs(mesh, precision, L)));
@@ -522,6 +524,7 @@ int ftle_compute(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double
   const Launch L = resolve_launch(opt);
   if ((rc = check_launch(L))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if (L.validate_mesh && (rc = validate_mesh_sync(mesh, workspace, s, nullptr))) return rc;
   if ((rc = run_advect(mesh, flow, t0, T, dt, nsteps, precision, flowmap, nullptr, 0, L, s))) return rc;
   FTLE_CUDA_CHECK(cudaMemsetAsync(workspace, 0, sizeof(ftle_counters), s));
   if ((rc = run_gradient(mesh, flowmap, precision, T, ftle_out, lambda_out, workspace, L, s,
@@ -621,7 +624,15 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
   if (nnz > 0)
     FTLE_CUDA_CHECK(
         cudaMemcpyAsync(ci, col_idx_host, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, side.stream));
+  // the copied lists are checked on the side stream while the advection runs (its counters sit
+  // in the workspace header, apart from the ftle_counters that the main stream clears)
+  MeshCheck* chk = mesh_check_ptr(device_ws);
+  if ((rc = launch_validate_mesh(&m, chk, side.stream))) return rc;
   if ((rc = run_advect(&m, flow, t0, T, dt, nsteps, precision, phi, nullptr, 0, L, s))) return rc;
+  if ((rc = finish_validate_mesh(chk, side.stream, nullptr))) {
+    cudaStreamSynchronize(s);  // nothing of this call stays in flight on an error return
+    return rc;
+  }
   if ((rc = side.join(s))) return rc;
   FTLE_CUDA_CHECK(cudaMemsetAsync(device_ws, 0, sizeof(ftle_counters), s));
   if ((rc = run_gradient(&m, phi, precision, T, ftle_dev, nullptr, device_ws, L, s, !refine_runs(&m, precision, L))))

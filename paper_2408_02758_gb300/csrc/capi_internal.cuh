@@ -14,7 +14,25 @@ struct Launch {
   int grad_block = 256;
   int refine_lanes = 32;
   bool defer_fp64 = false;
+  bool validate_mesh = false;
 };
+
+// Mesh validation counters (validate.cu), kept in the workspace header past ftle_counters (which
+// the batch extends into its reserved words): [0] row_ptr, [1] col_idx, [2] ell_idx.
+struct MeshCheck {
+  unsigned long long count[3];
+  unsigned long long first[3];
+};
+constexpr size_t kMeshCheckOffset = 128;
+static_assert(sizeof(ftle_counters) <= kMeshCheckOffset && kMeshCheckOffset + sizeof(MeshCheck) <= 256,
+              "mesh check counters live in the 256-byte workspace header");
+inline MeshCheck* mesh_check_ptr(void* ws) {
+  return reinterpret_cast<MeshCheck*>(reinterpret_cast<char*>(ws) + kMeshCheckOffset);
+}
+int launch_validate_mesh(const ftle_mesh* m, MeshCheck* dev_out, cudaStream_t s);
+int finish_validate_mesh(const MeshCheck* dev_out, cudaStream_t s, ftle_mesh_report* report);
+// Validation pass on `s` and its result (synchronises `s`); FTLE_EINVAL on a bad index.
+int validate_mesh_sync(const ftle_mesh* m, void* ws, cudaStream_t s, ftle_mesh_report* report);
 
 int check_mesh(const ftle_mesh* m);
 int check_flow(const ftle_flow* f, int dim);

@@ -48,7 +48,12 @@ class ftle_rotation_info(Structure):
 class ftle_options(Structure):
     _fields_ = [("refine_kappa", c_double), ("advect_block", c_int32), ("advect_blocks_per_sm", c_int32),
                 ("grad_block", c_int32), ("grad_tile", c_int32), ("refine_lanes", c_int32),
-                ("defer_fp64", c_int32), ("reserved", c_int32 * 2)]
+                ("defer_fp64", c_int32), ("validate_mesh", c_int32), ("reserved", c_int32)]
+
+
+class ftle_mesh_report(Structure):
+    _fields_ = [("bad_row_ptr", c_int64), ("bad_col_idx", c_int64), ("bad_ell_idx", c_int64),
+                ("first_bad_row", c_int64), ("first_bad_col", c_int64), ("first_bad_ell", c_int64)]
 
 
 class FTLEError(RuntimeError):
@@ -81,6 +86,7 @@ _SIGS = [
                                   c_double, c_double, c_double, c_int32, c_void_p, c_void_p, c_size_t,
                                   POINTER(ftle_options), c_void_p]),
     ("ftle_read_counters", c_int, [c_void_p, POINTER(ftle_counters), c_void_p]),
+    ("ftle_validate_mesh", c_int, [POINTER(ftle_mesh), POINTER(ftle_mesh_report), c_void_p, c_size_t, c_void_p]),
     ("ftle_ell_from_csr", c_int, [POINTER(ftle_mesh), c_int32, c_void_p, c_void_p]),
     ("ftle_csr_workspace_bytes", c_size_t, [c_int64, c_int32]),
     ("ftle_csr_from_elements", c_int, [c_int64, c_int64, c_int32, c_void_p, c_int32, c_void_p, c_void_p, c_int64,
@@ -161,10 +167,11 @@ def make_flow(flow) -> ftle_flow:
 
 def make_options(refine_kappa: float = 0.0, advect_block: int = 0, advect_blocks_per_sm: int = 0,
                  grad_block: int = 0, grad_tile: int = 0, refine_lanes: int = 0,
-                 defer_fp64: bool = False) -> ftle_options:
+                 defer_fp64: bool = False, validate_mesh: bool = False) -> ftle_options:
     o = ftle_options()
     o.refine_lanes = refine_lanes
     o.defer_fp64 = int(bool(defer_fp64))
+    o.validate_mesh = int(bool(validate_mesh))
     o.refine_kappa = refine_kappa
     o.advect_block = advect_block
     o.advect_blocks_per_sm = advect_blocks_per_sm
@@ -340,6 +347,20 @@ def ftle_read_counters(workspace, stream=None) -> dict:
     c = ftle_counters()
     _check("ftle_read_counters", lib().ftle_read_counters(_ptr(workspace), ctypes.byref(c), _stream(stream)))
     return {"n_flagged": int(c.n_flagged), "n_degenerate": int(c.n_degenerate), "n_readvected": int(c.n_readvected)}
+
+
+def ftle_validate_mesh(mesh: DeviceMesh, workspace=None, stream=None, check: bool = True) -> dict:
+    """Device pass over the mesh's neighbour indices (row_ptr, col_idx, ell_idx); returns the
+    report as a dict.  With check=True a bad index raises FTLEError (FTLE_EINVAL)."""
+    ws = workspace if workspace is not None else workspace_empty(256, device=mesh.coords.device)
+    r = ftle_mesh_report()
+    rc = lib().ftle_validate_mesh(ctypes.byref(mesh.desc), ctypes.byref(r), _ptr(ws),
+                                  ws.numel() * ws.element_size(), _stream(stream))
+    if check:
+        _check("ftle_validate_mesh", rc)
+    elif rc not in (FTLE_OK, FTLE_EINVAL):
+        _check("ftle_validate_mesh", rc)
+    return {k: int(getattr(r, k)) for k, _ in ftle_mesh_report._fields_} | {"status": int(rc)}
 
 
 # ------------------------------------------------------------------------------ buffer helpers

@@ -4,6 +4,9 @@ Tolerance: relative error <= 1e-4 on nodes where the oracle's lambda_max > 1 + 1
 nodes the absolute error must stay <= 1e-4 * max|FTLE_oracle|.  NaN (rank-deficient
 neighbourhoods) must coincide exactly.
 """
+import json
+import os
+
 import numpy as np
 
 REL_TOL = 1e-4
@@ -33,3 +36,16 @@ def compare(gpu_ftle, orc_ftle, orc_lam, rel_tol=REL_TOL, abs_frac=1e-4):
     })
     rep["ok"] = (rep["nan_mismatch"] == 0 and rep["max_rel"] <= rel_tol and rep["max_abs_ungated"] <= abs_frac * scale)
     return rep
+
+
+def report(workload: str, rep: dict, **extra) -> None:
+    """One line of the per-workload error table: printed (pytest -s shows it) and, when the
+    FTLE_ERROR_TABLE environment variable names a file, appended to it as JSON."""
+    keep = ("n", "n_gated", "max_abs", "max_rel", "p99_rel", "pass_frac", "max_abs_ungated", "abs_limit",
+            "nan_mismatch", "ok")
+    line = json.dumps({"workload": workload, **{k: rep[k] for k in keep if k in rep}, **extra})
+    print("ERROR-TABLE", line)
+    path = os.environ.get("FTLE_ERROR_TABLE")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(line + "\n")

@@ -9,6 +9,8 @@ import pytest
 import oracle as O
 from paper_2408_02758_gb300 import inputs as I
 
+from _parity import compare, report
+
 pytestmark = pytest.mark.gpu
 
 
@@ -37,7 +39,9 @@ def test_adjoint_matches_oracle_tangent_linear(scale, T, ckpt):
     g_orc, ft = O.param_grad(w.mesh.coords.astype(np.float64), w.mesh.row_ptr, w.mesh.col_idx, p0, T, w.dt, wts)
     rel = np.abs(g_gpu - g_orc) / np.maximum(np.abs(g_orc), 1e-3 * np.abs(g_orc).max())
     print("gpu", g_gpu, "oracle", g_orc, "rel", rel)
-    assert np.all(rel < 2e-3), (g_gpu, g_orc, rel)
+    # measured: <= 3e-5 for T <= 5, <= 3.7e-4 at T = 15 (1500 float adjoint steps)
+    tol = 5e-4 if abs(T) > 5 else 1e-4
+    assert np.all(rel < tol), (g_gpu, g_orc, rel)
     assert abs(loss.item() - float(wts @ ft)) < 1e-4 * abs(float(wts @ ft))
 
 
@@ -63,7 +67,8 @@ def test_adjoint_matches_oracle_central_differences():
         fp = O.ftle(O.DOUBLE_GYRE, p0 + e, x0, w.mesh.row_ptr, w.mesh.col_idx, T, w.dt)["ftle"]
         fm = O.ftle(O.DOUBLE_GYRE, p0 - e, x0, w.mesh.row_ptr, w.mesh.col_idx, T, w.dt)["ftle"]
         fd = (wts @ fp - wts @ fm) / (2 * h)
-        assert abs(params.grad[q].item() - fd) <= 3e-3 * max(abs(fd), 1e-2), (q, params.grad[q].item(), fd)
+        print(q, params.grad[q].item(), fd, abs(params.grad[q].item() - fd) / max(abs(fd), 1e-2))
+        assert abs(params.grad[q].item() - fd) <= 1e-4 * max(abs(fd), 1e-2), (q, params.grad[q].item(), fd)
 
 
 def test_backward_is_deterministic_and_validates():
@@ -92,3 +97,46 @@ def test_backward_is_deterministic_and_validates():
     with pytest.raises(ftle.FTLEError) as e:
         ftle.ftle_backward(dm, w.flow, 0.0, T, w.dt, "fp32c", phi, ck, 0, wt, outs[0].cuda(), ws)
     assert e.value.status == ftle.FTLE_EINVAL
+
+
+def test_adjoint_on_the_full_differentiable_workload():
+    """The differentiable workload itself: d(mean FTLE over x0 in [0.5, 1.5])/d(A, eps, omega) on
+    the 1024 x 512 jittered triangle mesh, T = 15, checkpoints every 50 steps, against the oracle's
+    forward-mode derivative and against central FP64 differences of the oracle (h = 1e-4)."""
+    import torch
+
+    from paper_2408_02758_gb300 import ftle
+    from paper_2408_02758_gb300.autograd import ftle_field
+
+    w = I.preset(4)
+    assert w.mesh.shape == (1024, 512) and w.T == 15.0 and w.extra["ckpt_every"] == 50
+    dm = ftle.DeviceMesh.from_mesh(w.mesh)
+    wts = w.extra["weights"].astype(np.float64)
+    assert abs(wts.sum() - 1.0) < 1e-12 and np.array_equal(wts > 0, _region_weights(w.mesh) > 0)
+    p0 = w.flow.params[:3].copy()
+    params = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    field = ftle_field(params, dm, w.T, w.dt, "fp32c", w.extra["ckpt_every"])
+    loss = (field.double().cpu() * torch.from_numpy(wts)).sum()
+    loss.backward()
+    g_gpu = params.grad.numpy()
+    x0 = w.mesh.coords.astype(np.float64)
+    g_orc, ft = O.param_grad(x0, w.mesh.row_ptr, w.mesh.col_idx, p0, w.T, w.dt, wts)
+    rel = np.abs(g_gpu - g_orc) / np.abs(g_orc)
+    h = 1e-4
+    fd = np.zeros(3)
+    for q in range(3):
+        e = np.zeros(3)
+        e[q] = h
+        fp = O.ftle(O.DOUBLE_GYRE, p0 + e, x0, w.mesh.row_ptr, w.mesh.col_idx, w.T, w.dt)["ftle"]
+        fm = O.ftle(O.DOUBLE_GYRE, p0 - e, x0, w.mesh.row_ptr, w.mesh.col_idx, w.T, w.dt)["ftle"]
+        fd[q] = (wts @ fp - wts @ fm) / (2 * h)
+    rel_fd = np.abs(g_gpu - fd) / np.abs(fd)
+    lam = O.ftle(O.DOUBLE_GYRE, p0, x0, w.mesh.row_ptr, w.mesh.col_idx, w.T, w.dt)["lam"]
+    rep = compare(field.detach().double().cpu().numpy(), ft, lam)
+    report(w.name, rep, sample="every node (forward field)", precision="fp32c", grad_gpu=g_gpu.tolist(),
+           grad_oracle_tangent=g_orc.tolist(), grad_central_fd=fd.tolist(), grad_max_rel_vs_tangent=float(rel.max()),
+           grad_max_rel_vs_fd=float(rel_fd.max()))
+    assert rep["ok"], rep
+    assert np.all(rel < 5e-4), (g_gpu, g_orc, rel)
+    assert np.all(rel_fd < 5e-4), (g_gpu, fd, rel_fd)
+    assert abs(loss.item() - float(wts @ ft)) < 1e-4 * abs(float(wts @ ft))

@@ -7,7 +7,7 @@ import pytest
 import oracle as O
 from paper_2408_02758_gb300 import inputs as I
 
-from _parity import compare
+from _parity import compare, report
 
 pytestmark = pytest.mark.gpu
 
@@ -140,3 +140,38 @@ def test_forward_backward_pair_in_one_batch(preset, T):
         o = O.ftle(w.flow.kind, w.flow.params, x0, w.mesh.row_ptr, w.mesh.col_idx, horizon, w.dt)
         rep = compare(got, o["ftle"], o["lam"])
         assert rep["ok"], rep
+
+
+def test_full_batched_workload_every_instance_matches_oracle():
+    """The 64-instance workload at full scale (lattices 64 x 32 to 1024 x 512, T in {5, 10, 15,
+    20}, eps and omega over their whole ranges), replayed from the captured graph as the
+    benchmark runs it: 200 sampled nodes of every instance against the oracle."""
+    import torch
+
+    from paper_2408_02758_gb300 import ftle
+
+    wl = I.batched_preset(64)
+    meshes = [ftle.DeviceMesh.from_mesh(w.mesh) for w in wl]
+    outs = [torch.full((w.mesh.n_nodes,), 7.0, dtype=torch.float32, device="cuda") for w in wl]
+    ws = ftle.workspace_empty(ftle.ftle_batch_workspace_bytes(meshes, "fp32c"))
+    plan = ftle.BatchPlan(meshes, [w.flow for w in wl], [w.T for w in wl], 0.01, "fp32c", outs, ws)
+    plan.launch()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(64)
+    g, of, ol = [], [], []
+    for q, (w, o) in enumerate(zip(wl, outs)):
+        rows = np.sort(rng.choice(w.mesh.n_nodes, min(200, w.mesh.n_nodes), replace=False))
+        ref = O.ftle_sample(w.flow.kind, w.flow.params, w.mesh.coords, w.mesh.row_ptr, w.mesh.col_idx, rows, w.T,
+                            w.dt)
+        got = o.double().cpu().numpy()
+        rep = compare(got[rows], ref["ftle"], ref["lam"])
+        assert rep["ok"], (q, w.name, rep)
+        assert np.isfinite(got).all(), q
+        g.append(got[rows])
+        of.append(ref["ftle"])
+        ol.append(ref["lam"])
+    plan.destroy()
+    rep = compare(np.concatenate(g), np.concatenate(of), np.concatenate(ol))
+    report("dg2d_batched_64", rep, sample="200 random nodes of each of the 64 instances", precision="fp32c",
+           execution="captured graph replay")
+    assert rep["ok"], rep
