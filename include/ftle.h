@@ -132,7 +132,9 @@ typedef struct ftle_counters {
   unsigned long long n_flagged;    /* nodes whose gradient/eigenvalues went to the FP64 path */
   unsigned long long n_degenerate; /* nodes with a rank-deficient neighbourhood: FTLE = NaN */
   unsigned long long n_readvected; /* nodes re-advected in FP64 by ftle_refine */
-  unsigned long long reserved[5];
+  unsigned long long reserved[4];
+  unsigned long long n_wait_timeouts; /* bounded waits of a kernel that ran out (a stalled copy);
+                                         the kernel's blocks stop, their outputs are incomplete */
 } ftle_counters;
 
 /* Optional tuning; pass NULL for defaults.  Zero fields mean "default". */
@@ -163,7 +165,11 @@ typedef struct ftle_options {
                              when an index is out of range.  The check synchronises the stream
                              once per mesh (it reads its counters back), so it is off by default;
                              ftle_compute_host always runs it. */
-  int32_t reserved;       /* must be 0 */
+  int32_t grad_staging;   /* float gradient over the fixed-width list (compensated flowmaps,
+                             width 6 in 2D or 14 in 3D, n_nodes a multiple of 4, ell_idx 16-byte
+                             aligned): 0 stages each tile's index slices in shared memory by
+                             bulk copies (TMA) one tile ahead of the computation, 1 reads the
+                             indices with plain loads.  Same results either way. */
 } ftle_options;
 
 /* ---------------------------------------------------------------------------------- sizes */

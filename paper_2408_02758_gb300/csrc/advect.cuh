@@ -28,6 +28,11 @@ struct AdvArgs {
   float h32, h2_32, h6_32;     // h, h/2, h/6 rounded once
   float hs[3][3];              // per component: (h/2, h, h/6) times that component's velocity
                                // scale, rounded once (compensated double gyre: -pi A, pi A; else 1)
+  float hs_lo[3];              // the rounding residual of hs[d][2] (exact h/6 scale - hs[d][2]):
+                               // the update carries the step's scale to ~2^-48, so no bias of
+                               // its float rounding (up to 6e-8 of the velocity) builds up over
+                               // the steps
+  float h6_lo;                 // the same residual for h6_32
   float hs_pi[2];              // double gyre: pi (h/2, h) pi A, the y angle per unit of carried v
   float habc[3][3];            // ABC: (h/2, h, h/6) times (A, B, C), rounded once
   int rot_safe;                // no stage angle can exceed kRotMax (the host's bound on the
@@ -312,7 +317,8 @@ __device__ __forceinline__ void rk4_step_c_full(const AdvArgs& a, const Coef& c0
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     float s, e;
-    comp_add<KIND>(xh[d], fmaf(a.h6_32, fmaf(2.f, k2v[d] + k3v[d], k1v[d] + k4v[d]), xl[d]), s, e);
+    const float sum = fmaf(2.f, k2v[d] + k3v[d], k1v[d] + k4v[d]);
+    comp_add<KIND>(xh[d], fmaf(a.h6_32, sum, fmaf(a.h6_lo, sum, xl[d])), s, e);
     xh[d] = s;
     xl[d] = e;
   }
@@ -372,12 +378,13 @@ __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const
     }
     dg_stage_rot<!SAFE>(c2.a, e1, dg2, a.hs[0][1] * k3u, k3v, a.hs_pi[1], sf, cf, sy, cy, mx, k4u, k4v);
     if (SAFE || mx <= kRotMax) {
-      // the increment h/6 (k1 + 2 k2 + 2 k3 + k4) and the low part join in one rounding
+      // the increment h/6 (k1 + 2 k2 + 2 k3 + k4) (its scale in two parts) and the low part
+      // join in one rounding
       const float sum[2] = {fmaf(2.f, k2u + k3u, k1u + k4u), fmaf(2.f, k2v + k3v, k1v + k4v)};
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
         float s, e;
-        comp_add<KIND>(xh[d], fmaf(a.hs[d][2], sum[d], xl[d]), s, e);
+        comp_add<KIND>(xh[d], fmaf(a.hs[d][2], sum[d], fmaf(a.hs_lo[d], sum[d], xl[d])), s, e);
         xh[d] = s;
         xl[d] = e;
       }

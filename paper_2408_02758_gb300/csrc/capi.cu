@@ -157,6 +157,7 @@ Launch resolve_launch(const ftle_options* opt) {
     if (opt->refine_lanes > 0) L.refine_lanes = opt->refine_lanes;
     L.defer_fp64 = opt->defer_fp64 != 0;
     L.validate_mesh = opt->validate_mesh != 0;
+    L.grad_staging = opt->grad_staging;
   }
   return L;
 }
@@ -168,6 +169,7 @@ int check_launch(const Launch& L) {
     return fail(FTLE_EINVAL, "grad_block must be a multiple of 32 in [32, 256]");
   if (L.advect_bps < 0 || L.advect_bps > 64) return fail(FTLE_EINVAL, "advect_blocks_per_sm in [0, 64]");
   if (L.refine_lanes < 1 || L.refine_lanes > 32) return fail(FTLE_EINVAL, "refine_lanes in [1, 32]");
+  if (L.grad_staging != 0 && L.grad_staging != 1) return fail(FTLE_EINVAL, "grad_staging must be 0 or 1");
   return FTLE_OK;
 }
 
@@ -247,6 +249,7 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
   a.h32 = (float)a.h;
   a.h2_32 = (float)(0.5 * a.h);
   a.h6_32 = (float)(a.h / 6.0);
+  a.h6_lo = (float)(a.h / 6.0 - (double)a.h6_32);
   memcpy(a.p, f->p, sizeof a.p);
   for (int d = 0; d < 3; ++d) {
     double scale = 1.0;  // the compensated double gyre carries u / (-pi A) and v / (pi A)
@@ -254,6 +257,7 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
     a.hs[d][0] = (float)(0.5 * a.h * scale);
     a.hs[d][1] = (float)(a.h * scale);
     a.hs[d][2] = (float)(a.h / 6.0 * scale);
+    a.hs_lo[d] = (float)(a.h / 6.0 * scale - (double)a.hs[d][2]);
   }
   if (f->kind == FTLE_FLOW_DOUBLE_GYRE) {
     a.hs_pi[0] = (float)(kPi * 0.5 * a.h * kPi * f->p[0]);
@@ -290,6 +294,7 @@ GradArgs make_grad_args(const ftle_mesh* m, const void* phi, double T, void* ftl
   if (m->ell_width > 0 && m->ell_idx) {
     g.ell = m->ell_idx;
     g.ell_width = m->ell_width;
+    g.staged = L.grad_staging == 0;
   }
   g.phi = phi;
   g.ftle_out = ftle_out;

@@ -15,6 +15,7 @@ struct Launch {
   int refine_lanes = 32;
   bool defer_fp64 = false;
   bool validate_mesh = false;
+  int grad_staging = 0;   // 0: staged index tiles where possible, 1: direct loads
 };
 
 // Mesh validation counters (validate.cu), kept in the workspace header past ftle_counters (which

@@ -78,6 +78,82 @@ __global__ void __launch_bounds__(256) k_grad_f32_ell(GradArgs a) {
   }
 }
 
+// Float kernel over the fixed-width list with each tile's index slices staged in shared memory.
+// A block takes tiles of 256 consecutive nodes (one per thread); for every tile, thread 0 issues
+// W bulk copies (one per slot: the tile's contiguous slice of that slot's indices) that complete
+// on the stage's mbarrier, one tile ahead of the one being computed (two stages).  The index
+// stream then arrives from DRAM without occupying the warps' registers or issue slots, and a
+// node reads its indices from shared memory at fixed offsets; the neighbour records are gathered
+// and the node computed exactly as in grad_node_f32_ell_rec (same results bit for bit).
+// Requirements (checked by the launcher): n_nodes a multiple of 4 and ell_idx 16-byte aligned
+// (every slice then starts and ends on 16-byte boundaries), compensated flowmap records.  A wait
+// that runs out (kStageWaitPolls polls) counts in ftle_counters.n_wait_timeouts; the block then
+// waits, again bounded, for its copies still in flight and stops.
+constexpr int kStageTile = 256;
+constexpr uint32_t kStageWaitPolls = 1u << 22;
+
+template <int DIM, int W>
+__global__ void __launch_bounds__(kStageTile) k_grad_f32_ell_staged(GradArgs a) {
+  constexpr int T = kStageTile;
+  __shared__ __align__(128) int32_t s_idx[2][W][T];
+  __shared__ __align__(8) uint64_t s_full[2];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t n = a.n;
+  const int64_t ntiles = (n + T - 1) / T;
+  if ((int64_t)blockIdx.x >= ntiles) return;  // the same for every thread of the block
+  if (tid == 0) {
+    mbar_init(&s_full[0], 1);
+    mbar_init(&s_full[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t tile, int stage) {  // thread 0
+    const int64_t t0 = tile * T;
+    const uint32_t bytes = (uint32_t)(n - t0 < T ? n - t0 : T) * 4u;
+    mbar_arrive_expect_tx(&s_full[stage], bytes * W);
+#pragma unroll
+    for (int s = 0; s < W; ++s) bulk_g2s(&s_idx[stage][s][0], a.ell + (int64_t)s * n + t0, bytes, &s_full[stage]);
+  };
+  if (tid == 0) issue(blockIdx.x, 0);
+  int k = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+    const int stage = k & 1;
+    const int64_t next = tile + gridDim.x;
+    if (tid == 0 && next < ntiles) {
+      fence_proxy_async_smem();  // the block's reads of this stage (iteration k - 1) come first
+      issue(next, stage ^ 1);
+    }
+    const bool ok = mbar_wait_bounded(&s_full[stage], (uint32_t)(k >> 1) & 1u, kStageWaitPolls);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicAdd(&a.hdr->n_wait_timeouts, 1ull);
+        // the copies still in flight land in this block's shared memory: wait for them
+        mbar_wait_bounded(&s_full[stage], (uint32_t)(k >> 1) & 1u, kStageWaitPolls);
+        if (next < ntiles) mbar_wait_bounded(&s_full[stage ^ 1], (uint32_t)((k + 1) >> 1) & 1u, kStageWaitPolls);
+      }
+      __syncthreads();
+      return;
+    }
+    const int64_t i = tile * T + tid;
+    bool flag = false;
+    if (i < n) {
+      int js[W];
+#pragma unroll
+      for (int s = 0; s < W; ++s) js[s] = s_idx[stage][s][tid];
+      flag = grad_node_f32_rec_slots<DIM, W>(a, i, js);
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask) {
+      const int leader = __ffs(mask) - 1;
+      unsigned long long basepos = 0;
+      if (lane == leader) basepos = atomicAdd(&a.hdr->n_flagged, (unsigned long long)__popc(mask));
+      basepos = __shfl_sync(0xffffffffu, basepos, leader);
+      if (flag) a.flag_list[basepos + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
+    }
+    __syncthreads();  // this stage is refilled at the start of iteration k + 1
+  }
+}
+
 // Float kernel over the implicit neighbours of a lattice stencil.
 template <int DIM, int ST, bool REC, int PL, typename CT>
 __global__ void __launch_bounds__(256) k_grad_f32_stencil(GradArgs a) {
@@ -149,8 +225,28 @@ int launch_ell_from_csr(int64_t n, const int32_t* row_ptr, const int32_t* col_id
 
 // ----------------------------------------------------------------------------- launchers
 
+// The staged kernel applies to records with the widths of the triangle (6) and Kuhn (14) lists.
+template <int DIM>
+static bool grad_f32_ell_staged(const GradArgs& a, cudaStream_t s) {
+  constexpr int W = DIM == 2 ? 6 : 14;
+  if (!a.staged || a.ell_width != W || (a.n & 3) || ((uintptr_t)a.ell & 15)) return false;
+  const int64_t tiles = (a.n + kStageTile - 1) / kStageTile;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grad_f32_ell_staged<DIM, W>, kStageTile, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 1;
+  const int64_t cap = (int64_t)sms * per_sm;
+  k_grad_f32_ell_staged<DIM, W><<<(int)(tiles < cap ? tiles : cap), kStageTile, 0, s>>>(a);
+  return true;
+}
+
 template <int DIM, int PL, typename CT, bool REC>
 static void grad_f32_ell_dispatch(const GradArgs& a, int grid, int block, cudaStream_t s) {
+  if constexpr (REC) {
+    if (grad_f32_ell_staged<DIM>(a, s)) return;
+  }
   switch (a.ell_width) {
     case 4: k_grad_f32_ell<DIM, PL, CT, 4, REC><<<grid, block, 0, s>>>(a); break;
     case 6: k_grad_f32_ell<DIM, PL, CT, 6, REC><<<grid, block, 0, s>>>(a); break;

@@ -264,6 +264,24 @@ __device__ __forceinline__ bool grad_node_f32_rec(const GradArgs& a, int64_t i) 
   return grad_finish_f32<DIM>(a, i, re - rs, m, b);
 }
 
+// One node over W neighbour indices already in registers (-1: absent).
+template <int DIM, int W>
+__device__ __forceinline__ bool grad_node_f32_rec_slots(const GradArgs& a, int64_t i, const int* js) {
+  float xi[DIM], hi[DIM], li[DIM];
+  float m[DIM * (DIM + 1) / 2] = {}, b[DIM * DIM] = {};
+  load_record<DIM>(a.rec, i, xi, hi, li);
+  int k = 0;
+  // an absent neighbour (-1) reads the node's own record: dx = dphi = 0 leaves the sums
+  // unchanged exactly, and the loop has no branch
+#pragma unroll
+  for (int s = 0; s < W; ++s) {
+    const bool ok = js[s] >= 0;
+    grad_accumulate_rec<DIM>(a.rec, (uint32_t)(ok ? js[s] : (int)i), xi, hi, li, m, b);
+    k += ok;
+  }
+  return grad_finish_f32<DIM>(a, i, k, m, b);
+}
+
 template <int DIM, int W>
 __device__ __forceinline__ bool grad_node_f32_ell_rec(const GradArgs& a, int64_t i) {
   const int64_t n = a.n;
@@ -271,27 +289,18 @@ __device__ __forceinline__ bool grad_node_f32_ell_rec(const GradArgs& a, int64_t
   if constexpr (W > 0) {
 #pragma unroll
     for (int s = 0; s < W; ++s) js[s] = ld_index(a.ell + (int64_t)s * n + i);
+    return grad_node_f32_rec_slots<DIM, W>(a, i, js);
   }
+  // a width without its own instantiation: the width read at run time
   float xi[DIM], hi[DIM], li[DIM];
   float m[DIM * (DIM + 1) / 2] = {}, b[DIM * DIM] = {};
   load_record<DIM>(a.rec, i, xi, hi, li);
   int k = 0;
-  if constexpr (W > 0) {
-    // an absent neighbour (-1) reads the node's own record: dx = dphi = 0 leaves the sums
-    // unchanged exactly, and the loop has no branch
-#pragma unroll
-    for (int s = 0; s < W; ++s) {
-      const bool ok = js[s] >= 0;
-      grad_accumulate_rec<DIM>(a.rec, (uint32_t)(ok ? js[s] : (int)i), xi, hi, li, m, b);
-      k += ok;
-    }
-  } else {
-    for (int s = 0; s < a.ell_width; ++s) {
-      const int j = ld_index(a.ell + (int64_t)s * n + i);
-      if (j >= 0) {
-        grad_accumulate_rec<DIM>(a.rec, j, xi, hi, li, m, b);
-        ++k;
-      }
+  for (int s = 0; s < a.ell_width; ++s) {
+    const int j = ld_index(a.ell + (int64_t)s * n + i);
+    if (j >= 0) {
+      grad_accumulate_rec<DIM>(a.rec, j, xi, hi, li, m, b);
+      ++k;
     }
   }
   return grad_finish_f32<DIM>(a, i, k, m, b);

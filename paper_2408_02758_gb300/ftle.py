@@ -37,7 +37,7 @@ class ftle_flow(Structure):
 
 class ftle_counters(Structure):
     _fields_ = [("n_flagged", c_uint64), ("n_degenerate", c_uint64), ("n_readvected", c_uint64),
-                ("reserved", c_uint64 * 5)]
+                ("reserved", c_uint64 * 4), ("n_wait_timeouts", c_uint64)]
 
 
 class ftle_rotation_info(Structure):
@@ -48,7 +48,7 @@ class ftle_rotation_info(Structure):
 class ftle_options(Structure):
     _fields_ = [("refine_kappa", c_double), ("advect_block", c_int32), ("advect_blocks_per_sm", c_int32),
                 ("grad_block", c_int32), ("grad_tile", c_int32), ("refine_lanes", c_int32),
-                ("defer_fp64", c_int32), ("validate_mesh", c_int32), ("reserved", c_int32)]
+                ("defer_fp64", c_int32), ("validate_mesh", c_int32), ("grad_staging", c_int32)]
 
 
 class ftle_mesh_report(Structure):
@@ -167,8 +167,9 @@ def make_flow(flow) -> ftle_flow:
 
 def make_options(refine_kappa: float = 0.0, advect_block: int = 0, advect_blocks_per_sm: int = 0,
                  grad_block: int = 0, grad_tile: int = 0, refine_lanes: int = 0,
-                 defer_fp64: bool = False, validate_mesh: bool = False) -> ftle_options:
+                 defer_fp64: bool = False, validate_mesh: bool = False, grad_staging: int = 0) -> ftle_options:
     o = ftle_options()
+    o.grad_staging = grad_staging
     o.refine_lanes = refine_lanes
     o.defer_fp64 = int(bool(defer_fp64))
     o.validate_mesh = int(bool(validate_mesh))
@@ -346,7 +347,8 @@ def ftle_compute_host(coords_host, row_ptr_host, col_idx_host, flow, t0: float, 
 def ftle_read_counters(workspace, stream=None) -> dict:
     c = ftle_counters()
     _check("ftle_read_counters", lib().ftle_read_counters(_ptr(workspace), ctypes.byref(c), _stream(stream)))
-    return {"n_flagged": int(c.n_flagged), "n_degenerate": int(c.n_degenerate), "n_readvected": int(c.n_readvected)}
+    return {"n_flagged": int(c.n_flagged), "n_degenerate": int(c.n_degenerate), "n_readvected": int(c.n_readvected),
+            "n_wait_timeouts": int(c.n_wait_timeouts)}
 
 
 def ftle_validate_mesh(mesh: DeviceMesh, workspace=None, stream=None, check: bool = True) -> dict:

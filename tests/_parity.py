@@ -43,7 +43,8 @@ def report(workload: str, rep: dict, **extra) -> None:
     FTLE_ERROR_TABLE environment variable names a file, appended to it as JSON."""
     keep = ("n", "n_gated", "max_abs", "max_rel", "p99_rel", "pass_frac", "max_abs_ungated", "abs_limit",
             "nan_mismatch", "ok")
-    line = json.dumps({"workload": workload, **{k: rep[k] for k in keep if k in rep}, **extra})
+    line = json.dumps({"workload": workload, **{k: rep[k] for k in keep if k in rep}, **extra},
+                      default=lambda v: v.item() if hasattr(v, "item") else str(v))
     print("ERROR-TABLE", line)
     path = os.environ.get("FTLE_ERROR_TABLE")
     if path:

@@ -102,7 +102,15 @@ def test_backward_is_deterministic_and_validates():
 def test_adjoint_on_the_full_differentiable_workload():
     """The differentiable workload itself: d(mean FTLE over x0 in [0.5, 1.5])/d(A, eps, omega) on
     the 1024 x 512 jittered triangle mesh, T = 15, checkpoints every 50 steps, against the oracle's
-    forward-mode derivative and against central FP64 differences of the oracle (h = 1e-4)."""
+    forward-mode derivative (5e-4 relative), with the forward field against the oracle at the
+    parity tolerance on every node.
+
+    Central FP64 differences of the oracle (h = 1e-4) are computed and reported, not asserted: at
+    this size and horizon the region mean is rough on the scale of h (ridge nodes whose FTLE moves
+    steeply with the parameters), and the oracle's own central differences approach its
+    forward-mode derivative only as h shrinks (for eps: 49 % off at h = 1e-4, 26 % at 1e-5, 8 % at
+    1e-6, 0.13 % at 1e-7).  The test of the smaller mesh at T = 4 holds the adjoint to central
+    differences at h = 1e-4, where they have converged."""
     import torch
 
     from paper_2408_02758_gb300 import ftle
@@ -138,5 +146,4 @@ def test_adjoint_on_the_full_differentiable_workload():
            grad_max_rel_vs_fd=float(rel_fd.max()))
     assert rep["ok"], rep
     assert np.all(rel < 5e-4), (g_gpu, g_orc, rel)
-    assert np.all(rel_fd < 5e-4), (g_gpu, fd, rel_fd)
     assert abs(loss.item() - float(wts @ ft)) < 1e-4 * abs(float(wts @ ft))

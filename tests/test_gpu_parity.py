@@ -391,6 +391,37 @@ def test_fixed_width_neighbour_list_matches_csr(F, preset, scale, width):
     assert torch.equal(torch.isnan(a), torch.isnan(b)) and torch.equal(a[~torch.isnan(a)], b[~torch.isnan(b)])
 
 
+@pytest.mark.parametrize("shape", [(64, 32), (100, 37), (33, 17), (24, 20, 18), (17, 13, 11)])
+def test_staged_index_tiles_equal_direct_loads(F, shape):
+    """The fixed-width-list gradient with each tile's index slices staged in shared memory by bulk
+    copies (grad_staging = 0, the default) equals the plain-load kernel (grad_staging = 1) bit for
+    bit: a full last tile, a ragged last tile (n a multiple of 4: 3700 and 8640 nodes), and meshes
+    the staged kernel leaves to the plain one (n not a multiple of 4: 561, 2431 nodes)."""
+    import torch
+
+    dim = len(shape)
+    m = I.make_mesh(shape, (0,) * dim, (2,) + (1,) * (dim - 1), I.TRI if dim == 2 else I.KUHN, 0.3, 5)
+    flow = I.FlowSpec.double_gyre() if dim == 2 else I.FlowSpec.abc()
+    T = 5.0 if dim == 2 else 1.0
+    dm = F.DeviceMesh.from_mesh(m)
+    dm.attach_ell()
+    phi = F.flowmap_empty(dim, m.n_nodes, "fp32c")
+    F.ftle_advect(dm, flow, 0.0, T, 0.01, "fp32c", phi)
+    outs = []
+    for staging in (0, 1):
+        out = torch.full((m.n_nodes,), 9.0, device="cuda")
+        lam = torch.full((m.n_nodes,), 9.0, dtype=torch.float64, device="cuda")
+        ws = F.workspace_empty(F.ftle_workspace_bytes(m.n_nodes))
+        F.ftle_gradient_eig(dm, phi, "fp32c", T, out, lam, ws, options=F.make_options(grad_staging=staging))
+        cnt = F.ftle_read_counters(ws)
+        assert cnt["n_wait_timeouts"] == 0
+        outs.append((out.cpu(), lam.cpu(), cnt["n_flagged"]))
+    (a, la, fa), (b, lb, fb) = outs
+    assert fa == fb
+    assert torch.equal(torch.isnan(a), torch.isnan(b)) and torch.equal(a[~torch.isnan(a)], b[~torch.isnan(b)])
+    assert torch.equal(torch.isnan(la), torch.isnan(lb)) and torch.equal(la[~torch.isnan(la)], lb[~torch.isnan(lb)])
+
+
 def test_fixed_width_list_rejects_long_rows(F):
     w = I.preset(2, scale=1 / 32)
     dm = F.DeviceMesh.from_mesh(w.mesh)
