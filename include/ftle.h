@@ -170,6 +170,11 @@ typedef struct ftle_options {
                              aligned): 0 stages each tile's index slices in shared memory by
                              bulk copies (TMA) one tile ahead of the computation, 1 reads the
                              indices with plain loads.  Same results either way. */
+  int32_t abc_refresh;    /* compensated ABC advection with the unchecked step (ftle_rotation_bounds
+                             .unchecked): stage one's sines and cosines of the state are evaluated
+                             afresh every abc_refresh steps and, in between, carried from the
+                             previous step and turned by its increment (a power of two in
+                             [1, 1024]; default 8; 1 evaluates them at every step). */
 } ftle_options;
 
 /* ---------------------------------------------------------------------------------- sizes */

@@ -14,6 +14,7 @@ enum Prec { P64 = 0, P32 = 1, P32C = 2 };
 enum Out { O64 = 0, O32 = 1, O32PAIR = 2 };
 
 constexpr int kAdvChunk = 2048;  // steps per coefficient-table chunk (2*chunk+1 half steps)
+constexpr int kAbcRefreshDefault = 8;  // AdvArgs::abc_refresh unless ftle_options sets it
 
 struct AdvArgs {
   int64_t n;                   // nodes (or list capacity when `list` is set)
@@ -35,6 +36,9 @@ struct AdvArgs {
   float h6_lo;                 // the same residual for h6_32
   float hs_pi[2];              // double gyre: pi (h/2, h) pi A, the y angle per unit of carried v
   float habc[3][3];            // ABC: (h/2, h, h/6) times (A, B, C), rounded once
+  int abc_refresh;             // compensated ABC, unchecked steps: stage one's sines and cosines
+                               // evaluated afresh every abc_refresh steps (a power of two),
+                               // carried and turned by each step's increment in between
   int rot_safe;                // no stage angle can exceed kRotMax (the host's bound on the
                                // increments; for the double gyre, of nodes in [0, 2] x [0, 1]),
                                // so the steps skip the angle check
@@ -324,6 +328,72 @@ __device__ __forceinline__ void rk4_step_c_full(const AdvArgs& a, const Coef& c0
   }
 }
 
+// The compensated ABC step from stage one's (sin, cos) of x, y, z at the state, (s0, c0):
+// stage increments d1 = h/2 k1, d2 = h/2 k2, d3 = h k3 and e4 = h/6 k4 straight from the folded
+// constants; the state's increment h/6 (k1 + 2 k2 + 2 k3 + k4) = (d1 + 2 d2 + d3) / 3 + e4 goes
+// to inc.  Stage two turns stage one's pairs by d1; stage three turns stage two's by d2 - d1 to
+// first order (|d2 - d1| <= h^2/4 L U for a flow with Lipschitz constant L and speed bound U, so
+// the dropped (d2 - d1)^2 / 2 stays near float rounding: kTinyMax); stage four turns stage one's
+// by d3.  Without SAFE a stage angle beyond the turns' limits returns false (the caller then
+// evaluates the step in full).
+template <bool SAFE>
+__device__ __forceinline__ bool abc_step_from(const AdvArgs& a, const float* s0, const float* c0v, float* inc) {
+  float d1[3], d2[3], d3[3], e4[3], mx = 0.0f;
+  d1[0] = fmaf(a.habc[0][0], s0[2], a.habc[0][2] * c0v[1]);
+  d1[1] = fmaf(a.habc[0][1], s0[0], a.habc[0][0] * c0v[2]);
+  d1[2] = fmaf(a.habc[0][2], s0[1], a.habc[0][1] * c0v[0]);
+  float s2[3], c2v[3];
+  rotate_small_xyz(s0, c0v, d1, s2, c2v);
+  abc_stage_k(a.habc[0], s2, c2v, d2);
+  {
+    float s3[3], c3[3], dmax = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float dd = d2[q] - d1[q];
+      if constexpr (!SAFE) dmax = fmaxf(dmax, fabsf(dd));
+      s3[q] = fmaf(c2v[q], dd, s2[q]);
+      c3[q] = fmaf(-s2[q], dd, c2v[q]);
+    }
+    if constexpr (!SAFE)
+      mx = fmaxf(fmaxf(mx, fmaxf(fabsf(d1[0]), fmaxf(fabsf(d1[1]), fabsf(d1[2])))), dmax * (kRotMax / kTinyMax));
+    abc_stage_k(a.habc[1], s3, c3, d3);
+  }
+  abc_stage_rot<!SAFE>(a.habc[2], d3, s0, c0v, mx, e4);
+  if (!(SAFE || mx <= kRotMax)) return false;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) inc[q] = fmaf(fmaf(2.f, d2[q], d1[q] + d3[q]), 1.0f / 3.0f, e4[q]);
+  return true;
+}
+
+// Stage one's (sin, cos) of the state carried from step to step by the unchecked compensated ABC
+// step (AdvArgs::rot_safe): a step whose index is a multiple of AdvArgs::abc_refresh evaluates
+// them afresh at the compensated state (fsincos_c); the steps between turn the previous step's
+// pairs by that step's increment (|inc| <= |h| U <= kRotMax, the same third-order turn as the
+// stages; the increment before its low part joins the state, which moves the angle by at most
+// half an ulp of the increment).  The turns' roundings accumulate over at most abc_refresh - 1
+// steps before the next fresh evaluation.
+struct AbcCarry {
+  float s[3], c[3];
+};
+
+__device__ __forceinline__ void abc_step_carried(const AdvArgs& a, int k, float* xh, float* xl, AbcCarry& cy) {
+  const int mask = a.abc_refresh - 1;  // abc_refresh is a power of two
+  if ((k & mask) == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) fsincos_c(xh[q], xl[q], cy.s[q], cy.c[q]);
+  }
+  float inc[3];
+  abc_step_from<true>(a, cy.s, cy.c, inc);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    float s, e;
+    comp_add<FTLE_FLOW_ABC>(xh[q], inc[q] + xl[q], s, e);
+    xh[q] = s;
+    xl[q] = e;
+  }
+  if (((k + 1) & mask) != 0) rotate_small_xyz(cy.s, cy.c, inc, cy.s, cy.c);
+}
+
 // Advance one node by one classic RK4 step (stages at t, t + h/2, t + h/2, t + h, with the
 // coefficients c0, c1, c2 of those half steps).  P64 updates xd; P32 updates xh; P32C updates
 // the compensated pair (xh, xl), evaluating the velocity at compensated stage points.  SAFE
@@ -392,41 +462,14 @@ __device__ __forceinline__ void rk4_step(const AdvArgs& a, const Coef& c0, const
       rk4_step_c_full<KIND, DIM>(a, c0, c1, c2, xh, xl);
     }
   } else if constexpr (KIND == FTLE_FLOW_ABC) {  // P32C, stages two to four by rotation
-    // stage increments d1 = h/2 k1, d2 = h/2 k2, d3 = h k3 and e4 = h/6 k4 straight from the
-    // folded constants; the step adds (d1 + 2 d2 + d3) / 3 + e4 = h/6 (k1 + 2 k2 + 2 k3 + k4)
-    float s0[3], c0v[3], d1[3], d2[3], d3[3], e4[3], mx = 0.0f;
+    float s0[3], c0v[3], inc[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) fsincos_c(xh[q], xl[q], s0[q], c0v[q]);
-    d1[0] = fmaf(a.habc[0][0], s0[2], a.habc[0][2] * c0v[1]);
-    d1[1] = fmaf(a.habc[0][1], s0[0], a.habc[0][0] * c0v[2]);
-    d1[2] = fmaf(a.habc[0][2], s0[1], a.habc[0][1] * c0v[0]);
-    // stage two turns stage one's pairs by d1; stage three turns stage two's by d2 - d1 to first
-    // order (|d2 - d1| <= h^2/4 L U for a flow with Lipschitz constant L and speed bound U, so
-    // the dropped (d2 - d1)^2 / 2 stays near float rounding: kTinyMax); stage four turns stage
-    // one's by d3
-    float s2[3], c2v[3];
-    rotate_small_xyz(s0, c0v, d1, s2, c2v);
-    abc_stage_k(a.habc[0], s2, c2v, d2);
-    {
-      float s3[3], c3[3], dmax = 0.0f;
+    if (abc_step_from<SAFE>(a, s0, c0v, inc)) {
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const float dd = d2[q] - d1[q];
-        if constexpr (!SAFE) dmax = fmaxf(dmax, fabsf(dd));
-        s3[q] = fmaf(c2v[q], dd, s2[q]);
-        c3[q] = fmaf(-s2[q], dd, c2v[q]);
-      }
-      if constexpr (!SAFE)
-        mx = fmaxf(fmaxf(mx, fmaxf(fabsf(d1[0]), fmaxf(fabsf(d1[1]), fabsf(d1[2])))), dmax * (kRotMax / kTinyMax));
-      abc_stage_k(a.habc[1], s3, c3, d3);
-    }
-    abc_stage_rot<!SAFE>(a.habc[2], d3, s0, c0v, mx, e4);
-    if (SAFE || mx <= kRotMax) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const float inc = fmaf(fmaf(2.f, d2[q], d1[q] + d3[q]), 1.0f / 3.0f, e4[q]);
         float s, e;
-        comp_add<KIND>(xh[q], inc + xl[q], s, e);
+        comp_add<KIND>(xh[q], inc[q] + xl[q], s, e);
         xh[q] = s;
         xl[q] = e;
       }
@@ -513,6 +556,7 @@ __global__ void __launch_bounds__(256, PREC == P32C ? 5 : 1) k_advect(AdvArgs a)
     if constexpr (KIND == FTLE_FLOW_DOUBLE_GYRE && PREC == P32C) safe_node = dg_node_safe(a, xd[0], xd[1]);
     int ck_left = a.ckpt_every;
     int ck_slot = 1;
+    AbcCarry carry;  // stage one's carried (sin, cos), refreshed at step 0 and every abc_refresh
     constexpr bool kSegs = PREC == P32C && OUT == O32PAIR && DIM == 2;
     int seg_slot = 0, next_seg = a.seg_len;
 
@@ -537,7 +581,10 @@ __global__ void __launch_bounds__(256, PREC == P32C ? 5 : 1) k_advect(AdvArgs a)
             const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
             const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
             const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
-            rk4_step<KIND, DIM, PREC, decltype(safe)::value>(a, c0, c1, c2, xh, xl, xd);
+            if constexpr (KIND == FTLE_FLOW_ABC && PREC == P32C && decltype(safe)::value)
+              abc_step_carried(a, k, xh, xl, carry);
+            else
+              rk4_step<KIND, DIM, PREC, decltype(safe)::value>(a, c0, c1, c2, xh, xl, xd);
             if (a.ckpt) {
               if (--ck_left == 0) {
                 ck_left = a.ckpt_every;

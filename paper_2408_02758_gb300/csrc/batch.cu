@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(256, PREC == P32C ? 4 : 1) k_batch_advect(cons
     // run-boundary states of compensated 2D flowmaps (as k_advect stores them)
     constexpr bool kSegs = PREC == P32C && OUT == O32PAIR && DIM == 2;
     int seg_slot = 0, next_seg = a.seg_len;
+    AbcCarry carry;  // as k_advect: the same steps, the same bits
     for (int ch = 0; ch < nchunks; ++ch) {
       const int k0 = ch * kAdvChunk;
       const int k1 = min(a.nsteps, k0 + kAdvChunk);
@@ -83,7 +84,10 @@ __global__ void __launch_bounds__(256, PREC == P32C ? 4 : 1) k_batch_advect(cons
             const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
             const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
             const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
-            rk4_step<KIND, DIM, PREC, decltype(safe)::value>(a, c0, c1, c2, xh, xl, xd);
+            if constexpr (KIND == FTLE_FLOW_ABC && PREC == P32C && decltype(safe)::value)
+              abc_step_carried(a, k, xh, xl, carry);
+            else
+              rk4_step<KIND, DIM, PREC, decltype(safe)::value>(a, c0, c1, c2, xh, xl, xd);
           }
         };
         // the unchecked steps exactly where k_advect takes them (dg_node_safe; ABC: rot_safe)
@@ -343,6 +347,7 @@ int plan_batch(int32_t n_inst, const ftle_mesh* meshes, const ftle_flow* flows, 
     memset(&bi, 0, sizeof bi);
     void* phi = P.ws + P.L.phi_off[q];
     bi.adv = make_adv_args(&meshes[q], &flows[q], 0.0, T[q], dt, nsteps);
+    bi.adv.abc_refresh = Lc.abc_refresh;
     bi.adv.out = phi;
     if (precision == FTLE_PREC_FP32C && meshes[q].dim == 2) {
       bi.adv.seg = reinterpret_cast<float2*>(reinterpret_cast<char*>(phi) + seg_offset(2, meshes[q].n_nodes));

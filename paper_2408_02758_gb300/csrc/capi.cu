@@ -158,6 +158,7 @@ Launch resolve_launch(const ftle_options* opt) {
     L.defer_fp64 = opt->defer_fp64 != 0;
     L.validate_mesh = opt->validate_mesh != 0;
     L.grad_staging = opt->grad_staging;
+    if (opt->abc_refresh != 0) L.abc_refresh = opt->abc_refresh;
   }
   return L;
 }
@@ -170,6 +171,8 @@ int check_launch(const Launch& L) {
   if (L.advect_bps < 0 || L.advect_bps > 64) return fail(FTLE_EINVAL, "advect_blocks_per_sm in [0, 64]");
   if (L.refine_lanes < 1 || L.refine_lanes > 32) return fail(FTLE_EINVAL, "refine_lanes in [1, 32]");
   if (L.grad_staging != 0 && L.grad_staging != 1) return fail(FTLE_EINVAL, "grad_staging must be 0 or 1");
+  if (L.abc_refresh < 1 || L.abc_refresh > 1024 || (L.abc_refresh & (L.abc_refresh - 1)))
+    return fail(FTLE_EINVAL, "abc_refresh must be a power of two in [1, 1024]");
   return FTLE_OK;
 }
 
@@ -268,6 +271,7 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
     for (int q = 0; q < 3; ++q) a.habc[s][q] = (float)(hsc[s] * f->p[q]);
   double angle, diff;
   if (rotation_bounds(f, a.h, &angle, &diff)) a.rot_safe = rotation_unchecked(angle, diff) ? 1 : 0;
+  a.abc_refresh = kAbcRefreshDefault;
   return a;
 }
 
@@ -384,6 +388,7 @@ int run_advect(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
                int precision, void* phi, void* ckpt, int ckpt_every, const Launch& L, cudaStream_t s) {
   if (m->n_nodes == 0) return FTLE_OK;
   AdvArgs a = make_adv_args(m, fl, t0, T, dt, nsteps);
+  a.abc_refresh = L.abc_refresh;
   a.out = phi;
   a.ckpt = ckpt;
   a.ckpt_every = ckpt ? ckpt_every : 0;

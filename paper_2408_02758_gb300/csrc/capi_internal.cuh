@@ -16,6 +16,7 @@ struct Launch {
   bool defer_fp64 = false;
   bool validate_mesh = false;
   int grad_staging = 0;   // 0: staged index tiles where possible, 1: direct loads
+  int abc_refresh = kAbcRefreshDefault;
 };
 
 // Mesh validation counters (validate.cu), kept in the workspace header past ftle_counters (which

@@ -48,7 +48,8 @@ class ftle_rotation_info(Structure):
 class ftle_options(Structure):
     _fields_ = [("refine_kappa", c_double), ("advect_block", c_int32), ("advect_blocks_per_sm", c_int32),
                 ("grad_block", c_int32), ("grad_tile", c_int32), ("refine_lanes", c_int32),
-                ("defer_fp64", c_int32), ("validate_mesh", c_int32), ("grad_staging", c_int32)]
+                ("defer_fp64", c_int32), ("validate_mesh", c_int32), ("grad_staging", c_int32),
+                ("abc_refresh", c_int32)]
 
 
 class ftle_mesh_report(Structure):
@@ -167,8 +168,10 @@ def make_flow(flow) -> ftle_flow:
 
 def make_options(refine_kappa: float = 0.0, advect_block: int = 0, advect_blocks_per_sm: int = 0,
                  grad_block: int = 0, grad_tile: int = 0, refine_lanes: int = 0,
-                 defer_fp64: bool = False, validate_mesh: bool = False, grad_staging: int = 0) -> ftle_options:
+                 defer_fp64: bool = False, validate_mesh: bool = False, grad_staging: int = 0,
+                 abc_refresh: int = 0) -> ftle_options:
     o = ftle_options()
+    o.abc_refresh = abc_refresh
     o.grad_staging = grad_staging
     o.refine_lanes = refine_lanes
     o.defer_fp64 = int(bool(defer_fp64))

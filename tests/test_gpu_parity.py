@@ -422,6 +422,41 @@ def test_staged_index_tiles_equal_direct_loads(F, shape):
     assert torch.equal(torch.isnan(la), torch.isnan(lb)) and torch.equal(la[~torch.isnan(la)], lb[~torch.isnan(lb)])
 
 
+@pytest.mark.parametrize("refresh", [1, 2, 8, 16])
+def test_abc_carried_stage_one_refresh(F, refresh):
+    """The compensated ABC step carries stage one's sines and cosines from step to step, turned by
+    each step's increment and evaluated afresh every abc_refresh steps: every period follows the
+    oracle at the parity tolerance (a ragged 500 steps against periods that do not divide it), and
+    the batched kernel, carrying them the same way, gives the single kernel's flowmap bit for bit."""
+    import torch
+
+    w = I.preset(2, scale=3 / 32)  # 24^3 jittered Kuhn mesh
+    opt = F.make_options(abc_refresh=refresh)
+    ft, lam, phi, cnt = run_gpu(F, w.mesh, w.flow, w.T, w.dt, "fp32c", options=opt)
+    o = _oracle_full(w.mesh, w.flow, w.T, w.dt)
+    rep = compare(ft, o["ftle"], o["lam"])
+    assert rep["ok"], (refresh, rep)
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    out = torch.full((w.mesh.n_nodes,), 3.0, device="cuda")
+    ws = F.workspace_empty(F.ftle_batch_workspace_bytes([dm], "fp32c"))
+    F.ftle_batch([dm], [w.flow], [w.T], w.dt, "fp32c", [out], ws, options=F.make_options(abc_refresh=refresh,
+                                                                                            refine_kappa=-1.0))
+    single = F.compute(dm, w.flow, w.T, w.dt, "fp32c", options=F.make_options(abc_refresh=refresh, refine_kappa=-1.0))
+    torch.cuda.synchronize()
+    a, b = out.cpu(), single.cpu()
+    assert torch.equal(torch.isnan(a), torch.isnan(b)) and torch.equal(a[~torch.isnan(a)], b[~torch.isnan(b)])
+
+
+def test_abc_refresh_must_be_a_power_of_two(F):
+    w = I.preset(2, scale=1 / 32)
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    phi = F.flowmap_empty(3, w.mesh.n_nodes, "fp32c")
+    for bad in (3, 2048, -4):
+        with pytest.raises(F.FTLEError) as e:
+            F.ftle_advect(dm, w.flow, 0.0, 1.0, w.dt, "fp32c", phi, options=F.make_options(abc_refresh=bad))
+        assert e.value.status == F.FTLE_EINVAL
+
+
 def test_fixed_width_list_rejects_long_rows(F):
     w = I.preset(2, scale=1 / 32)
     dm = F.DeviceMesh.from_mesh(w.mesh)
