@@ -524,7 +524,9 @@ __device__ __forceinline__ bool dg_node_safe(const AdvArgs& a, double x, double 
 // on the full meshes with the paired rotations, the double gyre runs 15.84 ms at 40 registers
 // (six blocks), 15.47 at 48 and 15.83 at 64 (four); the ABC flow (stage-two pairing alone)
 // 44.84 ms at 40 and 44.11 at 47.
-template <int KIND, int DIM, int PREC, int OUT, typename CT, bool SAFE = false>
+// CARRY (with SAFE, the compensated ABC step): stage one's (sin, cos) carried across steps
+// (abc_step_carried, AdvArgs::abc_refresh > 1).
+template <int KIND, int DIM, int PREC, int OUT, typename CT, bool SAFE = false, bool CARRY = false>
 __global__ void __launch_bounds__(256, PREC == P32C ? 5 : 1) k_advect(AdvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kTable = (KIND == FTLE_FLOW_DOUBLE_GYRE);
@@ -575,13 +577,15 @@ __global__ void __launch_bounds__(256, PREC == P32C ? 5 : 1) k_advect(AdvArgs a)
       for (int k = k0; k < k1;) {
         // steps up to the next run boundary (uniform across the block), then its state
         const int stop = (kSegs && a.seg) ? min(k1, next_seg) : k1;
-        auto steps = [&](auto safe) {
+        // abc_refresh = 1 takes rk4_step's unchecked ABC step (CARRY false), the same arithmetic
+        // without the carried pairs' bookkeeping
+        auto steps = [&](auto safe, auto carried) {
           for (; k < stop; ++k) {
             const int m = 2 * (k - k0);
             const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
             const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
             const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
-            if constexpr (KIND == FTLE_FLOW_ABC && PREC == P32C && decltype(safe)::value)
+            if constexpr (KIND == FTLE_FLOW_ABC && PREC == P32C && decltype(safe)::value && decltype(carried)::value)
               abc_step_carried(a, k, xh, xl, carry);
             else
               rk4_step<KIND, DIM, PREC, decltype(safe)::value>(a, c0, c1, c2, xh, xl, xd);
@@ -596,12 +600,13 @@ __global__ void __launch_bounds__(256, PREC == P32C ? 5 : 1) k_advect(AdvArgs a)
             }
           }
         };
-        if (SAFE)
-          steps(std::integral_constant<bool, SAFE>{});
-        else if (safe_node)
-          steps(std::true_type{});
-        else
-          steps(std::false_type{});
+        if (SAFE) {
+          steps(std::integral_constant<bool, SAFE>{}, std::integral_constant<bool, CARRY>{});
+        } else if (safe_node) {
+          steps(std::true_type{}, std::false_type{});
+        } else {
+          steps(std::false_type{}, std::false_type{});
+        }
         if constexpr (kSegs) {
           if (a.seg && k == next_seg) {
             if (seg_slot < kSegments - 1)

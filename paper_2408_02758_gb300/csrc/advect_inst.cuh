@@ -12,8 +12,11 @@ int launch_advect_typed(int prec, int out, const AdvArgs& args, int grid, int bl
   } else if (prec == P32 && out == O32) {
     k_advect<KIND, DIM, P32, O32, CT><<<grid, block, smem, stream>>>(args);
   } else if (prec == P32C && out == O32PAIR) {
-    if (KIND == FTLE_FLOW_ABC && args.rot_safe)
-      k_advect<KIND, DIM, P32C, O32PAIR, CT, KIND == FTLE_FLOW_ABC><<<grid, block, smem, stream>>>(args);
+    constexpr bool kAbc = KIND == FTLE_FLOW_ABC;
+    if (kAbc && args.rot_safe && args.abc_refresh > 1)
+      k_advect<KIND, DIM, P32C, O32PAIR, CT, kAbc, kAbc><<<grid, block, smem, stream>>>(args);
+    else if (kAbc && args.rot_safe)
+      k_advect<KIND, DIM, P32C, O32PAIR, CT, kAbc><<<grid, block, smem, stream>>>(args);
     else
       k_advect<KIND, DIM, P32C, O32PAIR, CT><<<grid, block, smem, stream>>>(args);
   } else if (prec == P64 && out == O32PAIR) {

@@ -78,23 +78,26 @@ __global__ void __launch_bounds__(256, PREC == P32C ? 4 : 1) k_batch_advect(cons
       if (!active) continue;
       for (int k = k0; k < k1;) {
         const int stop = (kSegs && a.seg) ? min(k1, next_seg) : k1;
-        auto steps = [&](auto safe) {
+        auto steps = [&](auto safe, auto carried) {
           for (; k < stop; ++k) {
             const int m = 2 * (k - k0);
             const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
             const Coef c1 = coef_at<KIND, PREC>(tab32, tab64, m + 1);
             const Coef c2 = coef_at<KIND, PREC>(tab32, tab64, m + 2);
-            if constexpr (KIND == FTLE_FLOW_ABC && PREC == P32C && decltype(safe)::value)
+            if constexpr (KIND == FTLE_FLOW_ABC && PREC == P32C && decltype(safe)::value && decltype(carried)::value)
               abc_step_carried(a, k, xh, xl, carry);
             else
               rk4_step<KIND, DIM, PREC, decltype(safe)::value>(a, c0, c1, c2, xh, xl, xd);
           }
         };
-        // the unchecked steps exactly where k_advect takes them (dg_node_safe; ABC: rot_safe)
-        if (safe)
-          steps(std::true_type{});
+        // the unchecked steps exactly where k_advect takes them (dg_node_safe; ABC: rot_safe),
+        // stage one carried as k_advect carries it
+        if (safe && a.abc_refresh > 1)
+          steps(std::true_type{}, std::true_type{});
+        else if (safe)
+          steps(std::true_type{}, std::false_type{});
         else
-          steps(std::false_type{});
+          steps(std::false_type{}, std::false_type{});
         if constexpr (kSegs) {
           if (a.seg && k == next_seg) {
             if (seg_slot < kSegments - 1)

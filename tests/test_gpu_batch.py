@@ -7,7 +7,7 @@ import pytest
 import oracle as O
 from paper_2408_02758_gb300 import inputs as I
 
-from _parity import compare, report
+from _parity import compare, compare_conditioned, float_sensitivity, report
 
 pytestmark = pytest.mark.gpu
 
@@ -170,8 +170,20 @@ def test_full_batched_workload_every_instance_matches_oracle():
         g.append(got[rows])
         of.append(ref["ftle"])
         ol.append(ref["lam"])
-    plan.destroy()
     rep = compare(np.concatenate(g), np.concatenate(of), np.concatenate(ol))
     report("dg2d_batched_64", rep, sample="200 random nodes of each of the 64 instances", precision="fp32c",
            execution="captured graph replay")
     assert rep["ok"], rep
+    # whole fields of two instances with ill-conditioned ridge flanks (T = 15 on 1024 x 512,
+    # T = 20 on 512 x 256): every node within 1e-4, or within the oracle's own change under a
+    # one-rounding change of a flow parameter
+    for q in (2, 3):
+        w = wl[q]
+        assert w.mesh.n_nodes in (524288, 131072) and w.T in (15.0, 20.0), (q, w.name, w.T)
+        ref = O.ftle(w.flow.kind, w.flow.params, w.mesh.coords, w.mesh.row_ptr, w.mesh.col_idx, w.T, w.dt)
+        S = float_sensitivity(O, w.flow, w.mesh, w.T, w.dt, base=ref["ftle"])
+        rep = compare_conditioned(outs[q].double().cpu().numpy(), ref["ftle"], ref["lam"], S)
+        report(w.name, rep, sample="every node", precision="fp32c", execution="captured graph replay",
+               eps=float(w.flow.params[1]), omega=float(w.flow.params[2]), T=w.T)
+        assert rep["ok"], (q, rep)
+    plan.destroy()

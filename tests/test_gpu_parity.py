@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 from paper_2408_02758_gb300 import inputs as I
 
-from _parity import compare, report
+from _parity import compare, compare_conditioned, float_sensitivity, report
 
 pytestmark = pytest.mark.gpu
 
@@ -208,6 +208,21 @@ def test_full_size_workload_sampled(F, idx, layout):
     assert rep["ok"], (rep, cnt)
     assert np.isfinite(ft).all()
     assert cnt["n_degenerate"] == 0
+
+
+def test_full_field_triangle_double_gyre(F):
+    """Every node of the 2048 x 1024 triangle-mesh workload (the benchmark's layout) against the
+    oracle's whole field: 1e-4 relative on gated nodes, or the oracle's own one-rounding
+    sensitivity where that is larger."""
+    w, dm, _, _ = _full_size(1)
+    dm.detach_stencil().attach_ell()
+    ft = F.compute(dm, w.flow, w.T, w.dt, w.precision).double().cpu().numpy()
+    dm.detach_ell()
+    ref = O.ftle(w.flow.kind, w.flow.params, w.mesh.coords, w.mesh.row_ptr, w.mesh.col_idx, w.T, w.dt)
+    S = float_sensitivity(O, w.flow, w.mesh, w.T, w.dt, base=ref["ftle"])
+    rep = compare_conditioned(ft, ref["ftle"], ref["lam"], S)
+    report(w.name, rep, sample="every node", precision=w.precision, neighbours="ell")
+    assert rep["ok"], rep
 
 
 # ----------------------------------------------------------------------------- edge cases
