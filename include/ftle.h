@@ -269,7 +269,11 @@ int ftle_compute(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double
  * ftle_host (float, or double for FP64) and synchronises `stream` before returning.  The
  * copied lists always go through ftle_validate_mesh (on a second stream, while the advection
  * runs): an index out of range returns FTLE_EINVAL before any kernel reads through it.
- * Host buffers should be pinned for full copy bandwidth.  device_ws must hold
+ * Page-locked host buffers that the device can address (cudaHostAlloc, cudaMallocHost or
+ * cudaHostRegister with mapping) are used in place where that saves a copy: for FP32C the
+ * advection reads coords_host directly over the host link, and the kernels write the FTLE into
+ * ftle_host directly; other buffers (pageable memory) are staged through device_ws by copies.
+ * device_ws must hold
  * ftle_host_workspace_bytes(dim, n_nodes, nnz, precision) bytes. */
 size_t ftle_host_workspace_bytes(int32_t dim, int64_t n_nodes, int64_t nnz, int32_t precision);
 int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coords_host,

@@ -567,6 +567,19 @@ struct SideStream {
   }
 };
 
+// The device address of a host buffer the GPU can read and write in place (page-locked memory
+// mapped into the device's address space, e.g. from cudaHostAlloc): the kernels then reach it
+// over the host link without a staging copy.  NULL for anything else (pageable memory is
+// copied as before).
+static void* device_view(const void* host) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 size_t ftle_host_workspace_bytes(int32_t dim, int64_t n_nodes, int64_t nnz, int32_t precision) {
   if ((dim != 2 && dim != 3) || n_nodes < 0 || nnz < 0) return 0;
   const size_t cb = (precision == FTLE_PREC_FP64 ? sizeof(double) : sizeof(float)) * (size_t)dim * (size_t)n_nodes;
@@ -622,12 +635,20 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
   if (!isfinite(t0)) return fail(FTLE_EINVAL, "t0 must be finite");
   const Launch L = resolve_launch(opt);
   if ((rc = check_launch(L))) return rc;
+  // Page-locked, mapped host buffers are used in place: the advection reads each node's
+  // coordinates once over the host link (compensated float mode, where the gradient reads the
+  // flowmap's records and only the few FP64-path nodes read coordinates again), and the kernels
+  // write the FTLE straight into the caller's buffer; anything else goes through staging copies.
+  void* coords_view = precision == FTLE_PREC_FP32C && n_nodes > 0 ? device_view(coords_host) : nullptr;
+  void* out_view = n_nodes > 0 ? device_view(ftle_host) : nullptr;
+  if (coords_view) m.coords = coords_view;
+  if (out_view) ftle_dev = out_view;
   // The neighbour lists are needed only once the flowmap is done, so they cross on a side stream
   // while the advection (which needs the coordinates alone) runs.
   SideStream side;
   if ((rc = side.open(s))) return rc;
   if (n_nodes > 0) {
-    FTLE_CUDA_CHECK(cudaMemcpyAsync(coords, coords_host, cb, cudaMemcpyHostToDevice, s));
+    if (!coords_view) FTLE_CUDA_CHECK(cudaMemcpyAsync(coords, coords_host, cb, cudaMemcpyHostToDevice, s));
     FTLE_CUDA_CHECK(cudaMemcpyAsync(rp, row_ptr_host, sizeof(int32_t) * (size_t)(n_nodes + 1),
                                     cudaMemcpyHostToDevice, side.stream));
   }
@@ -648,7 +669,7 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
   if ((rc = run_gradient(&m, phi, precision, T, ftle_dev, nullptr, device_ws, L, s, !refine_runs(&m, precision, L))))
     return rc;
   if ((rc = run_refine(&m, flow, t0, T, dt, nsteps, precision, phi, ftle_dev, nullptr, device_ws, L, s))) return rc;
-  if (n_nodes > 0) FTLE_CUDA_CHECK(cudaMemcpyAsync(ftle_host, ftle_dev, ob, cudaMemcpyDeviceToHost, s));
+  if (n_nodes > 0 && !out_view) FTLE_CUDA_CHECK(cudaMemcpyAsync(ftle_host, ftle_dev, ob, cudaMemcpyDeviceToHost, s));
   FTLE_CUDA_CHECK(cudaStreamSynchronize(s));
   return FTLE_OK;
 }

@@ -220,6 +220,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // Orders this thread's earlier generic-proxy accesses of shared memory before later async-proxy
 // ones (a bulk copy refilling a buffer the block has just read).
 __device__ __forceinline__ void fence_proxy_async_smem() {

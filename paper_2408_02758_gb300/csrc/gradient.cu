@@ -81,14 +81,17 @@ __global__ void __launch_bounds__(256) k_grad_f32_ell(GradArgs a) {
 // Float kernel over the fixed-width list with each tile's index slices staged in shared memory.
 // A block takes tiles of 256 consecutive nodes (one per thread); for every tile, thread 0 issues
 // W bulk copies (one per slot: the tile's contiguous slice of that slot's indices) that complete
-// on the stage's mbarrier, one tile ahead of the one being computed (two stages).  The index
-// stream then arrives from DRAM without occupying the warps' registers or issue slots, and a
-// node reads its indices from shared memory at fixed offsets; the neighbour records are gathered
-// and the node computed exactly as in grad_node_f32_ell_rec (same results bit for bit).
-// Requirements (checked by the launcher): n_nodes a multiple of 4 and ell_idx 16-byte aligned
-// (every slice then starts and ends on 16-byte boundaries), compensated flowmap records.  A wait
-// that runs out (kStageWaitPolls polls) counts in ftle_counters.n_wait_timeouts; the block then
-// waits, again bounded, for its copies still in flight and stops.
+// on the stage's "full" mbarrier, one tile ahead of the one being computed (two stages).  The
+// index stream then arrives from DRAM without occupying the warps' registers or issue slots, and
+// a node reads its indices from shared memory at fixed offsets; the neighbour records are
+// gathered and the node computed exactly as in grad_node_f32_ell_rec (same results bit for bit).
+// Every thread releases a stage on its "empty" mbarrier once its indices are in registers, and
+// thread 0 refills the stage only after all 256 releases, so no block-wide barrier holds the
+// warps together: a warp runs up to a tile ahead of the slowest.  Requirements (checked by the
+// launcher): n_nodes a multiple of 4 and ell_idx 16-byte aligned (every slice then starts and
+// ends on 16-byte boundaries), compensated flowmap records.  Every wait is bounded
+// (kStageWaitPolls polls); a warp whose wait runs out counts in ftle_counters.n_wait_timeouts and
+// stops, thread 0 first waiting, again bounded, for the copy it still has in flight.
 constexpr int kStageTile = 256;
 constexpr uint32_t kStageWaitPolls = 1u << 22;
 
@@ -96,14 +99,16 @@ template <int DIM, int W>
 __global__ void __launch_bounds__(kStageTile) k_grad_f32_ell_staged(GradArgs a) {
   constexpr int T = kStageTile;
   __shared__ __align__(128) int32_t s_idx[2][W][T];
-  __shared__ __align__(8) uint64_t s_full[2];
+  __shared__ __align__(8) uint64_t s_full[2], s_empty[2];
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t n = a.n;
   const int64_t ntiles = (n + T - 1) / T;
   if ((int64_t)blockIdx.x >= ntiles) return;  // the same for every thread of the block
   if (tid == 0) {
-    mbar_init(&s_full[0], 1);
-    mbar_init(&s_full[1], 1);
+    for (int st = 0; st < 2; ++st) {
+      mbar_init(&s_full[st], 1);
+      mbar_init(&s_empty[st], T);
+    }
     mbar_init_fence();
   }
   __syncthreads();
@@ -119,29 +124,32 @@ __global__ void __launch_bounds__(kStageTile) k_grad_f32_ell_staged(GradArgs a) 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
     const int stage = k & 1;
     const int64_t next = tile + gridDim.x;
+    bool ok = true, issued = false;
     if (tid == 0 && next < ntiles) {
-      fence_proxy_async_smem();  // the block's reads of this stage (iteration k - 1) come first
-      issue(next, stage ^ 1);
-    }
-    const bool ok = mbar_wait_bounded(&s_full[stage], (uint32_t)(k >> 1) & 1u, kStageWaitPolls);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicAdd(&a.hdr->n_wait_timeouts, 1ull);
-        // the copies still in flight land in this block's shared memory: wait for them
-        mbar_wait_bounded(&s_full[stage], (uint32_t)(k >> 1) & 1u, kStageWaitPolls);
-        if (next < ntiles) mbar_wait_bounded(&s_full[stage ^ 1], (uint32_t)((k + 1) >> 1) & 1u, kStageWaitPolls);
+      // the other stage was read in iteration k - 1: refill it once every thread released it
+      if (k >= 1) ok = mbar_wait_bounded(&s_empty[stage ^ 1], (uint32_t)((k - 1) >> 1) & 1u, kStageWaitPolls);
+      if (ok) {
+        fence_proxy_async_smem();
+        issue(next, stage ^ 1);
+        issued = true;
       }
-      __syncthreads();
-      return;
+    }
+    if (ok) ok = mbar_wait_bounded(&s_full[stage], (uint32_t)(k >> 1) & 1u, kStageWaitPolls);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) atomicAdd(&a.hdr->n_wait_timeouts, 1ull);
+      if (tid == 0) {
+        // the copies this block still has in flight land in its shared memory: wait for them
+        mbar_wait_bounded(&s_full[stage], (uint32_t)(k >> 1) & 1u, kStageWaitPolls);
+        if (issued) mbar_wait_bounded(&s_full[stage ^ 1], (uint32_t)((k + 1) >> 1) & 1u, kStageWaitPolls);
+      }
+      break;
     }
     const int64_t i = tile * T + tid;
-    bool flag = false;
-    if (i < n) {
-      int js[W];
+    int js[W];
 #pragma unroll
-      for (int s = 0; s < W; ++s) js[s] = s_idx[stage][s][tid];
-      flag = grad_node_f32_rec_slots<DIM, W>(a, i, js);
-    }
+    for (int s = 0; s < W; ++s) js[s] = s_idx[stage][s][tid];
+    mbar_arrive(&s_empty[stage]);
+    const bool flag = i < n && grad_node_f32_rec_slots<DIM, W>(a, i, js);
     const unsigned mask = __ballot_sync(0xffffffffu, flag);
     if (mask) {
       const int leader = __ffs(mask) - 1;
@@ -150,7 +158,6 @@ __global__ void __launch_bounds__(kStageTile) k_grad_f32_ell_staged(GradArgs a) 
       basepos = __shfl_sync(0xffffffffu, basepos, leader);
       if (flag) a.flag_list[basepos + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
     }
-    __syncthreads();  // this stage is refilled at the start of iteration k + 1
   }
 }
 

@@ -305,6 +305,36 @@ def test_host_entry_point_matches_device_entry_point(F):
     assert np.array_equal(out.double().numpy(), dev)
 
 
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_host_entry_point_pinned_in_place_equals_staged(F, prec):
+    """Page-locked buffers are read and written in place by the kernels (coordinates in FP32C, the
+    FTLE always); pageable buffers go through staging copies: the same field bit for bit, and the
+    device path's field."""
+    import torch
+
+    w = I.preset(2, scale=1 / 16) if prec == "fp32c" else I.preset(1, scale=1 / 32)
+    mesh = w.mesh
+    coords = mesh.coords.astype(np.float64) if prec == "fp64" else mesh.coords
+    dim, n = mesh.dim, mesh.n_nodes
+    ws = F.workspace_empty(F.ftle_host_workspace_bytes(dim, n, mesh.nnz, prec))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    outs = []
+    for pinned in (True, False):
+        ch = torch.from_numpy(np.ascontiguousarray(coords))
+        rp = torch.from_numpy(mesh.row_ptr)
+        ci = torch.from_numpy(mesh.col_idx)
+        out = torch.full((n,), 5.0, dtype=dt)
+        if pinned:
+            ch, rp, ci, out = ch.pin_memory(), rp.pin_memory(), ci.pin_memory(), out.pin_memory()
+        F.ftle_compute_host(ch, rp, ci, w.flow, 0.0, w.T, w.dt, prec, out, ws)
+        outs.append(out.numpy().copy())
+    assert np.array_equal(outs[0], outs[1], equal_nan=True)
+    dm = F.DeviceMesh(torch.from_numpy(np.ascontiguousarray(coords)).cuda(), torch.from_numpy(mesh.row_ptr).cuda(),
+                      torch.from_numpy(mesh.col_idx).cuda())
+    dev = F.compute(dm, w.flow, w.T, w.dt, prec).cpu().numpy()
+    assert np.array_equal(outs[0], dev, equal_nan=True)
+
+
 def test_invalid_arguments_raise(F):
     import torch
 
