@@ -174,12 +174,12 @@ def test_full_batched_workload_every_instance_matches_oracle():
     report("dg2d_batched_64", rep, sample="200 random nodes of each of the 64 instances", precision="fp32c",
            execution="captured graph replay")
     assert rep["ok"], rep
-    # whole fields of two instances with ill-conditioned ridge flanks (T = 15 on 1024 x 512,
-    # T = 20 on 512 x 256): every node within 1e-4, or within the oracle's own change under a
+    # whole fields of the three instances with the most ill-conditioned ridge flanks (T = 20,
+    # 512 x 256 lattices): every node within 1e-4, or within the oracle's own change under a
     # one-rounding change of a flow parameter
-    for q in (2, 3):
+    for q in (24, 5, 8):
         w = wl[q]
-        assert w.mesh.n_nodes in (524288, 131072) and w.T in (15.0, 20.0), (q, w.name, w.T)
+        assert w.T == 20.0, (q, w.name, w.T)
         ref = O.ftle(w.flow.kind, w.flow.params, w.mesh.coords, w.mesh.row_ptr, w.mesh.col_idx, w.T, w.dt)
         S = float_sensitivity(O, w.flow, w.mesh, w.T, w.dt, base=ref["ftle"])
         rep = compare_conditioned(outs[q].double().cpu().numpy(), ref["ftle"], ref["lam"], S)
