@@ -631,11 +631,16 @@ def main():
                      "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                     "(max SM clock of measured peaks)",
                      "flops_per_point_step": FLOPS_PER_POINT_STEP[kind], "ms": adv_ms,
-                     "traffic": traffic.get("k_advect")},
+                     "traffic": traffic.get("k_advect"), "target_frac": 0.60,
+                     "target_met": achieved / peak >= 0.60,
+                     "measure": "algorithmic flops of the step as implemented / time (ncu's FP32-pipe busy "
+                                "fraction, higher, is in profiles/)"},
         "roofline_gradient": {"kernel": "gradient stage (float gradient kernel + counter memset; the flagged nodes' FP64 pass runs in the refine stage)", "bound": "hbm",
                               "achieved": grad_bytes / (grad_ms / 1000.0) / 1e9, "peak": peaks.get("hbm_gbs"),
                               "unit": "GB/s", "frac": grad_bytes / (grad_ms / 1000.0) / 1e9 / peaks.get("hbm_gbs", 6800.0),
-                              "bytes_per_launch": grad_bytes, "ms": grad_ms, "traffic": traffic.get("k_grad_f32")},
+                              "bytes_per_launch": grad_bytes, "ms": grad_ms, "traffic": traffic.get("k_grad_f32"),
+                              "target_frac": 0.70,
+                              "target_met": grad_bytes / (grad_ms / 1000.0) / 1e9 / peaks.get("hbm_gbs", 6800.0) >= 0.70},
         "stage_ms": {"advect": adv_ms, "gradient": grad_ms, "refine": statistics.mean(t_ref),
                      "wall_per_step_incl_flush": 1000 * t_wall / K},
         "counters": counters,

@@ -19,7 +19,9 @@ from pathlib import Path
 from typing import Callable, Iterable
 
 ADVECT_CANDIDATES = [(256, 32), (256, 8), (128, 16), (64, 32), (256, 4), (128, 64)]
-GRAD_CANDIDATES = [128, 256]
+# gradient: the staged fixed-width-list kernel (fixed 256-thread tiles; the plain kernels where it
+# does not apply) or plain loads with 128 / 256 threads per block
+GRAD_CANDIDATES = [{"grad_staging": 0}, {"grad_block": 128, "grad_staging": 1}, {"grad_block": 256, "grad_staging": 1}]
 BATCH_TILE_CANDIDATES = [(256, 256), (128, 512), (256, 1024), (64, 256)]
 
 
@@ -118,7 +120,8 @@ def params_for_compute(mesh, flow, T: float, dt: float, precision: str = "fp32c"
 
     cache = cache or Cache()
     n_steps = int(round(abs(T) / dt))
-    key = shape_key(_gpu_name(), "compute", mesh.dim, int(flow.kind), precision, mesh.n_nodes, n_steps)
+    layout = "stencil" if mesh.desc.stencil else ("ell" if mesh.desc.ell_width else "csr")
+    key = shape_key(_gpu_name(), f"compute-{layout}", mesh.dim, int(flow.kind), precision, mesh.n_nodes, n_steps)
     ch = None if retune else cache.get(key)
     if ch is None:
         phi = ftle.flowmap_empty(mesh.dim, mesh.n_nodes, precision)
@@ -132,10 +135,10 @@ def params_for_compute(mesh, flow, T: float, dt: float, precision: str = "fp32c"
         adv = pick([{"advect_block": b, "advect_blocks_per_sm": s} for b, s in ADVECT_CANDIDATES], t_adv)
 
         def t_grad(c):
-            o = ftle.make_options(grad_block=c["grad_block"])
+            o = ftle.make_options(**c)
             return _event_timer(lambda: ftle.ftle_gradient_eig(mesh, phi, precision, T, out, None, ws, options=o))
 
-        gr = pick([{"grad_block": b} for b in GRAD_CANDIDATES], t_grad)
+        gr = pick(GRAD_CANDIDATES, t_grad)
         ch = Choice({**adv.params, **gr.params}, adv.ms + gr.ms)
         cache.put(key, ch)
     return dict(ch.params)
