@@ -265,16 +265,15 @@ __device__ __forceinline__ void abc_stage_k(const float* co, const float* s, con
   k[2] = fmaf(co[2], s[1], co[1] * c[0]);
 }
 
-// rotate_small of the (sin, cos) pairs of x, y and z by the angles d: x and y as one paired
-// rotation, z alone.
+// rotate_small of the (sin, cos) pairs of x, y and z by the angles d, three scalar rotations.
+// With stage one carried across steps the ABC step is held by the FP32 pipe, not by issue, and a
+// paired f32x2 rotation of x and y (same bits) holds that pipe longer: 39.9 ms paired against
+// 38.5 ms scalar at 256^3 (it paid while the step was issue-bound: 45.2 -> 43.6 ms then).
 __device__ __forceinline__ void rotate_small_xyz(const float* s0, const float* c0, const float* d, float* s,
                                                  float* c) {
-  float2 sp, cp;
-  rotate_small2(make_float2(s0[0], s0[1]), make_float2(c0[0], c0[1]), make_float2(d[0], d[1]), sp, cp);
-  s[0] = sp.x;
-  s[1] = sp.y;
-  c[0] = cp.x;
-  c[1] = cp.y;
+  const float sx = s0[0], sy = s0[1], cx = c0[0], cy = c0[1];  // s and c may alias s0 and c0
+  rotate_small(sx, cx, d[0], s[0], c[0]);
+  rotate_small(sy, cy, d[1], s[1], c[1]);
   rotate_small(s0[2], c0[2], d[2], s[2], c[2]);
 }
 

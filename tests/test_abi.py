@@ -91,3 +91,39 @@ def test_status_strings_and_host_side_validation():
     assert L.ftle_gradient_eig(ctypes.byref(m3), None, 2, 1.0, None, None, None, 0, None, None) == ftle.FTLE_EINVAL
     assert b"flowmap" in L.ftle_last_error()
     assert L.ftle_workspace_bytes(1000) >= 8000
+
+
+def test_validate_mesh_host_side_errors():
+    """ftle_validate_mesh refuses a NULL mesh and a missing or misaligned workspace on the host,
+    before any device work."""
+    import ctypes
+
+    from paper_2408_02758_gb300 import ftle
+
+    L = ftle.lib()
+    rep = ftle.ftle_mesh_report()
+    assert L.ftle_validate_mesh(None, ctypes.byref(rep), None, 0, None) == ftle.FTLE_EINVAL
+    m = ftle.ftle_mesh()
+    m.dim = 2
+    m.n_nodes = 0
+    assert L.ftle_validate_mesh(ctypes.byref(m), ctypes.byref(rep), None, 0, None) == ftle.FTLE_EWORKSPACE
+    assert L.ftle_validate_mesh(ctypes.byref(m), ctypes.byref(rep), 256 + 8, 4096, None) == ftle.FTLE_EWORKSPACE
+
+
+def test_options_refuse_bad_staging_and_refresh():
+    """grad_staging outside {0, 1} and abc_refresh that is not a power of two in [1, 1024] are
+    refused on the host (the flow and mesh are checked first, then the options)."""
+    import ctypes
+
+    from paper_2408_02758_gb300 import ftle
+
+    L = ftle.lib()
+    f = ftle.ftle_flow()
+    f.kind = 1  # ABC
+    m = ftle.ftle_mesh()
+    m.dim = 3
+    m.n_nodes = 0
+    for kw in ({"grad_staging": 2}, {"abc_refresh": 3}, {"abc_refresh": 2048}):
+        o = ftle.make_options(**kw)
+        rc = L.ftle_advect(ctypes.byref(m), ctypes.byref(f), 0.0, 1.0, 0.01, 2, None, None, 0, ctypes.byref(o), None)
+        assert rc == ftle.FTLE_EINVAL, kw
