@@ -277,6 +277,19 @@ __device__ __forceinline__ void rotate_small_xyz(const float* s0, const float* c
   rotate_small(s0[2], c0[2], d[2], s[2], c[2]);
 }
 
+// The same three rotations with x and y as one paired f32x2 rotation (same bits).
+__device__ __forceinline__ void rotate_small_xyz_paired(const float* s0, const float* c0, const float* d, float* s,
+                                                        float* c) {
+  float2 sp, cp;
+  rotate_small2(make_float2(s0[0], s0[1]), make_float2(c0[0], c0[1]), make_float2(d[0], d[1]), sp, cp);
+  const float sz = s0[2], cz = c0[2];
+  s[0] = sp.x;
+  s[1] = sp.y;
+  c[0] = cp.x;
+  c[1] = cp.y;
+  rotate_small(sz, cz, d[2], s[2], c[2]);
+}
+
 // ABC stage two, three or four of the compensated step: stage one's (sin, cos) of x, y, z rotated
 // by the stage increments d (radians); with CHECK the largest increment joins `mx`.  co = (A, B, C) times
 // the scale of the value returned (the next stage's increment, or h/6 k4).
@@ -519,14 +532,14 @@ __device__ __forceinline__ bool dg_node_safe(const AdvArgs& a, double x, double 
 }
 
 // SAFE: the instantiation for AdvArgs::rot_safe (rk4_step's angle-check-free ABC step).  The
-// compensated float kernels are held to five 256-thread blocks per SM (48 registers): measured
-// on the full meshes with the paired rotations, the double gyre runs 15.84 ms at 40 registers
-// (six blocks), 15.47 at 48 and 15.83 at 64 (four); the ABC flow (stage-two pairing alone)
-// 44.84 ms at 40 and 44.11 at 47.
+// compensated float kernels are held to five 256-thread blocks per SM (48 registers) for the
+// double gyre (measured on the full mesh: 15.84 ms at 40 registers, six blocks; 15.47 at 48;
+// 15.83 at 64, four blocks) and six for the ABC flow with stage one carried (40 registers, a
+// few bytes spilled outside the step loop: 37.83 ms against 38.46 at five blocks).
 // CARRY (with SAFE, the compensated ABC step): stage one's (sin, cos) carried across steps
 // (abc_step_carried, AdvArgs::abc_refresh > 1).
 template <int KIND, int DIM, int PREC, int OUT, typename CT, bool SAFE = false, bool CARRY = false>
-__global__ void __launch_bounds__(256, PREC == P32C ? 5 : 1) k_advect(AdvArgs a) {
+__global__ void __launch_bounds__(256, PREC == P32C ? (KIND == FTLE_FLOW_ABC ? 6 : 5) : 1) k_advect(AdvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kTable = (KIND == FTLE_FLOW_DOUBLE_GYRE);
   float2* tab32 = reinterpret_cast<float2*>(smem_raw);
