@@ -388,12 +388,10 @@ struct AbcCarry {
   float s[3], c[3];
 };
 
-__device__ __forceinline__ void abc_step_carried(const AdvArgs& a, int k, float* xh, float* xl, AbcCarry& cy) {
-  const int mask = a.abc_refresh - 1;  // abc_refresh is a power of two
-  if ((k & mask) == 0) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) fsincos_c(xh[q], xl[q], cy.s[q], cy.c[q]);
-  }
+// One carried step from the pairs in cy: the step's increment, the compensated state update,
+// and (with TURN) the pairs turned by the increment for the next step.
+template <bool TURN>
+__device__ __forceinline__ void abc_carried_one(const AdvArgs& a, float* xh, float* xl, AbcCarry& cy) {
   float inc[3];
   abc_step_from<true>(a, cy.s, cy.c, inc);
 #pragma unroll
@@ -403,7 +401,39 @@ __device__ __forceinline__ void abc_step_carried(const AdvArgs& a, int k, float*
     xh[q] = s;
     xl[q] = e;
   }
-  if (((k + 1) & mask) != 0) rotate_small_xyz(cy.s, cy.c, inc, cy.s, cy.c);
+  if constexpr (TURN) rotate_small_xyz(cy.s, cy.c, inc, cy.s, cy.c);
+}
+
+__device__ __forceinline__ void abc_fresh_pairs(const float* xh, const float* xl, AbcCarry& cy) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q) fsincos_c(xh[q], xl[q], cy.s[q], cy.c[q]);
+}
+
+// Step k alone (for loops that do more per step, such as storing checkpoints).
+__device__ __forceinline__ void abc_step_carried(const AdvArgs& a, int k, float* xh, float* xl, AbcCarry& cy) {
+  const int mask = a.abc_refresh - 1;  // abc_refresh is a power of two
+  if ((k & mask) == 0) abc_fresh_pairs(xh, xl, cy);
+  if (((k + 1) & mask) != 0)
+    abc_carried_one<true>(a, xh, xl, cy);
+  else
+    abc_carried_one<false>(a, xh, xl, cy);
+}
+
+// Steps k .. stop - 1, the same arithmetic as abc_step_carried step by step, grouped between
+// refreshes so that the inner loop tests nothing but its bound (k ends at stop).
+__device__ __forceinline__ void abc_steps_carried(const AdvArgs& a, int& k, int stop, float* xh, float* xl,
+                                                  AbcCarry& cy) {
+  const int mask = a.abc_refresh - 1;
+  while (k < stop) {
+    const int g = min(stop, (k | mask) + 1);  // the next step that refreshes, or stop
+    if ((k & mask) == 0) abc_fresh_pairs(xh, xl, cy);
+    for (; k < g - 1; ++k) abc_carried_one<true>(a, xh, xl, cy);
+    if ((g & mask) != 0)  // cut short by stop: a later call carries on from these pairs
+      abc_carried_one<true>(a, xh, xl, cy);
+    else
+      abc_carried_one<false>(a, xh, xl, cy);
+    ++k;
+  }
 }
 
 // Advance one node by one classic RK4 step (stages at t, t + h/2, t + h/2, t + h, with the
@@ -592,6 +622,12 @@ __global__ void __launch_bounds__(256, PREC == P32C ? (KIND == FTLE_FLOW_ABC ? 6
         // abc_refresh = 1 takes rk4_step's unchecked ABC step (CARRY false), the same arithmetic
         // without the carried pairs' bookkeeping
         auto steps = [&](auto safe, auto carried) {
+          if constexpr (KIND == FTLE_FLOW_ABC && PREC == P32C && decltype(safe)::value && decltype(carried)::value) {
+            if (!a.ckpt) {
+              abc_steps_carried(a, k, stop, xh, xl, carry);
+              return;
+            }
+          }
           for (; k < stop; ++k) {
             const int m = 2 * (k - k0);
             const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);

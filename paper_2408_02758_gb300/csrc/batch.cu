@@ -79,6 +79,10 @@ __global__ void __launch_bounds__(256, PREC == P32C ? 4 : 1) k_batch_advect(cons
       for (int k = k0; k < k1;) {
         const int stop = (kSegs && a.seg) ? min(k1, next_seg) : k1;
         auto steps = [&](auto safe, auto carried) {
+          if constexpr (KIND == FTLE_FLOW_ABC && PREC == P32C && decltype(safe)::value && decltype(carried)::value) {
+            abc_steps_carried(a, k, stop, xh, xl, carry);
+            return;
+          }
           for (; k < stop; ++k) {
             const int m = 2 * (k - k0);
             const Coef c0 = coef_at<KIND, PREC>(tab32, tab64, m);
