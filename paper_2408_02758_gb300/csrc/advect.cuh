@@ -426,6 +426,15 @@ __device__ __forceinline__ void abc_steps_carried(const AdvArgs& a, int& k, int 
   const int mask = a.abc_refresh - 1;
   while (k < stop) {
     const int g = min(stop, (k | mask) + 1);  // the next step that refreshes, or stop
+    if (mask == kAbcRefreshDefault - 1 && (k & mask) == 0 && g - k == kAbcRefreshDefault) {
+      // a whole group of the default period, unrolled
+      abc_fresh_pairs(xh, xl, cy);
+#pragma unroll
+      for (int q = 0; q < kAbcRefreshDefault - 1; ++q) abc_carried_one<true>(a, xh, xl, cy);
+      abc_carried_one<false>(a, xh, xl, cy);
+      k = g;
+      continue;
+    }
     if ((k & mask) == 0) abc_fresh_pairs(xh, xl, cy);
     for (; k < g - 1; ++k) abc_carried_one<true>(a, xh, xl, cy);
     if ((g & mask) != 0)  // cut short by stop: a later call carries on from these pairs
