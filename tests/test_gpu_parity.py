@@ -492,6 +492,30 @@ def test_abc_carried_stage_one_refresh(F, refresh):
     assert torch.equal(torch.isnan(a), torch.isnan(b)) and torch.equal(a[~torch.isnan(a)], b[~torch.isnan(b)])
 
 
+@pytest.mark.parametrize("T", [5.0, 2.47, 23.0])
+def test_abc_carried_steps_with_and_without_checkpoints(F, T):
+    """The carried ABC steps run grouped between refreshes (a whole group of the default period
+    unrolled) when no checkpoint is stored, and one at a time when checkpoints are: the flowmap
+    is the same bit for bit, for step counts that end a group exactly, cut one short (247) and
+    span two coefficient chunks of 2048 steps (2300)."""
+    import torch
+
+    w = I.preset(2, scale=1 / 32)  # 8^3 jittered Kuhn mesh
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    n = w.mesh.n_nodes
+    nsteps = int(round(T / w.dt))
+    a = F.flowmap_empty(3, n, "fp32c")
+    b = F.flowmap_empty(3, n, "fp32c")
+    ck = F.checkpoints_empty(3, n, nsteps, 37, "fp32c")
+    F.ftle_advect(dm, w.flow, 0.0, T, w.dt, "fp32c", a)
+    F.ftle_advect(dm, w.flow, 0.0, T, w.dt, "fp32c", b, ck, 37)
+    torch.cuda.synchronize()
+    pa, pb = F.flowmap_pairs(a, 3, n), F.flowmap_pairs(b, 3, n)
+    assert torch.equal(pa, pb)
+    last = ck[nsteps // 37].view(3, n, 2)
+    assert torch.isfinite(last).all()
+
+
 def test_abc_refresh_must_be_a_power_of_two(F):
     w = I.preset(2, scale=1 / 32)
     dm = F.DeviceMesh.from_mesh(w.mesh)
