@@ -600,7 +600,9 @@ def main():
             te.append(time.perf_counter() - t0)
         h2d = ch.numel() * ch.element_size() + rp.numel() * 4 + ci.numel() * 4
         e2e = {"value": n / statistics.mean(te), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(oh.numel() * oh.element_size())}
+               "d2h_bytes_per_step": int(oh.numel() * oh.element_size()),
+               "ms_per_call": {"mean": 1e3 * statistics.mean(te), "median": 1e3 * statistics.median(te),
+                               "min": 1e3 * min(te), "max": 1e3 * max(te)}}
         del hws
 
     if rank != 0:
