@@ -293,12 +293,13 @@ GradArgs make_grad_args(const ftle_mesh* m, const void* phi, double T, void* ftl
   g.coords = m->coords;
   g.row_ptr = m->row_ptr;
   g.col_idx = m->col_idx;
+  g.nnz = m->nnz;
+  g.staged = L.grad_staging == 0;
   g.stencil = m->stencil;
   for (int q = 0; q < 3; ++q) g.grid[q] = (uint32_t)m->grid[q];
   if (m->ell_width > 0 && m->ell_idx) {
     g.ell = m->ell_idx;
     g.ell_width = m->ell_width;
-    g.staged = L.grad_staging == 0;
   }
   g.phi = phi;
   g.ftle_out = ftle_out;

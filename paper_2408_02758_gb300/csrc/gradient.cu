@@ -161,6 +161,117 @@ __global__ void __launch_bounds__(kStageTile) k_grad_f32_ell_staged(GradArgs a) 
   }
 }
 
+// Float kernel over CSR rows with each tile's stretch of col_idx staged in shared memory.  The
+// rows of a tile of 256 consecutive nodes are one contiguous stretch [row_ptr[t0],
+// row_ptr[t0 + 256]) of col_idx; thread 0 brings it into shared memory with one bulk copy a tile
+// ahead (two stages, mbarriers as in k_grad_f32_ell_staged), taking the row_ptr bounds it needs
+// from loads issued one tile earlier still, so that nothing waits on them.  The copy covers the
+// stretch from its start rounded down to a 16-byte boundary to its end rounded down likewise; a
+// node reads the few indices past that end (and every index of a stretch longer than a stage) from
+// global memory.  The per-node arithmetic and the neighbour order are grad_node_f32_rec's (same
+// results bit for bit).  The copy stays inside [0, nnz) whatever row_ptr holds; the gathers trust
+// the indices as the plain kernel does.
+constexpr int kCsrStageInts = 16 * kStageTile;  // indices per stage: 16 per node of a full tile
+
+template <int DIM>
+__global__ void __launch_bounds__(kStageTile) k_grad_f32_csr_staged(GradArgs a) {
+  constexpr int T = kStageTile;
+  __shared__ __align__(128) int32_t s_idx[2][kCsrStageInts];
+  __shared__ __align__(8) uint64_t s_full[2], s_empty[2];
+  __shared__ int64_t s_lo[2], s_hi[2];  // positions [lo, hi) of col_idx held by the stage
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t n = a.n;
+  const int64_t ntiles = (n + T - 1) / T;
+  if ((int64_t)blockIdx.x >= ntiles) return;  // the same for every thread of the block
+  if (tid == 0) {
+    for (int st = 0; st < 2; ++st) {
+      mbar_init(&s_full[st], 1);
+      mbar_init(&s_empty[st], T);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  // thread 0: the row_ptr bounds of a tile, loaded ahead of its copy
+  auto bounds = [&](int64_t tile, int64_t& lo, int64_t& hi) {
+    const int64_t t0 = tile * T, t1 = t0 + T < n ? t0 + T : n;
+    lo = __ldg(a.row_ptr + t0);
+    hi = __ldg(a.row_ptr + t1);
+  };
+  auto issue = [&](int stage, int64_t lo, int64_t hi) {  // thread 0
+    int64_t lo0 = lo & ~(int64_t)3, hi0 = hi & ~(int64_t)3;
+    if (lo0 < 0 || hi0 > a.nnz || hi0 <= lo0 || hi0 - lo0 > kCsrStageInts) hi0 = lo0 = lo;  // nothing staged
+    s_lo[stage] = lo0;
+    s_hi[stage] = hi0;
+    if (hi0 > lo0) {
+      const uint32_t bytes = (uint32_t)(hi0 - lo0) * 4u;
+      mbar_arrive_expect_tx(&s_full[stage], bytes);
+      bulk_g2s(&s_idx[stage][0], a.col_idx + lo0, bytes, &s_full[stage]);
+    } else {
+      mbar_arrive(&s_full[stage]);
+    }
+  };
+  int64_t plo = 0, phi = 0;  // thread 0: bounds of the next tile to issue
+  if (tid == 0) {
+    int64_t lo, hi;
+    bounds(blockIdx.x, lo, hi);
+    issue(0, lo, hi);
+    if ((int64_t)blockIdx.x + gridDim.x < ntiles) bounds(blockIdx.x + gridDim.x, plo, phi);
+  }
+  int k = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+    const int stage = k & 1;
+    const int64_t next = tile + gridDim.x;
+    bool ok = true, issued = false;
+    if (tid == 0 && next < ntiles) {
+      if (k >= 1) ok = mbar_wait_bounded(&s_empty[stage ^ 1], (uint32_t)((k - 1) >> 1) & 1u, kStageWaitPolls);
+      if (ok) {
+        fence_proxy_async_smem();
+        issue(stage ^ 1, plo, phi);
+        issued = true;
+        if (next + gridDim.x < ntiles) bounds(next + gridDim.x, plo, phi);
+      }
+    }
+    if (ok) ok = mbar_wait_bounded(&s_full[stage], (uint32_t)(k >> 1) & 1u, kStageWaitPolls);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) atomicAdd(&a.hdr->n_wait_timeouts, 1ull);
+      if (tid == 0) {
+        mbar_wait_bounded(&s_full[stage], (uint32_t)(k >> 1) & 1u, kStageWaitPolls);
+        if (issued) mbar_wait_bounded(&s_full[stage ^ 1], (uint32_t)((k + 1) >> 1) & 1u, kStageWaitPolls);
+      }
+      break;
+    }
+    const int64_t lo = s_lo[stage], hi = s_hi[stage];
+    const int64_t i = tile * T + tid;
+    int rs = 0, re = 0;
+    if (i < n) {
+      rs = __ldg(a.row_ptr + i);
+      re = __ldg(a.row_ptr + i + 1);
+    }
+    bool flag = false;
+    if (i < n) {
+      float xi[DIM], hi_[DIM], li[DIM];
+      float m[DIM * (DIM + 1) / 2] = {}, b[DIM * DIM] = {};
+      load_record<DIM>(a.rec, i, xi, hi_, li);
+      for (int e = rs; e < re; ++e) {
+        const int j = (e >= lo && e < hi) ? s_idx[stage][e - lo] : ld_index(a.col_idx + e);
+        grad_accumulate_rec<DIM>(a.rec, j, xi, hi_, li, m, b);
+      }
+      mbar_arrive(&s_empty[stage]);
+      flag = grad_finish_f32<DIM>(a, i, re - rs, m, b);
+    } else {
+      mbar_arrive(&s_empty[stage]);
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask) {
+      const int leader = __ffs(mask) - 1;
+      unsigned long long basepos = 0;
+      if (lane == leader) basepos = atomicAdd(&a.hdr->n_flagged, (unsigned long long)__popc(mask));
+      basepos = __shfl_sync(0xffffffffu, basepos, leader);
+      if (flag) a.flag_list[basepos + __popc(mask & ((1u << lane) - 1u))] = (int32_t)i;
+    }
+  }
+}
+
 // Float kernel over the implicit neighbours of a lattice stencil.
 template <int DIM, int ST, bool REC, int PL, typename CT>
 __global__ void __launch_bounds__(256) k_grad_f32_stencil(GradArgs a) {
@@ -249,6 +360,22 @@ static bool grad_f32_ell_staged(const GradArgs& a, cudaStream_t s) {
   return true;
 }
 
+// The staged CSR kernel applies to records over any rows (col_idx 16-byte aligned).
+template <int DIM>
+static bool grad_f32_csr_staged(const GradArgs& a, cudaStream_t s) {
+  if (!a.staged || a.nnz <= 0 || ((uintptr_t)a.col_idx & 15)) return false;
+  const int64_t tiles = (a.n + kStageTile - 1) / kStageTile;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grad_f32_csr_staged<DIM>, kStageTile, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int sms = device_sm_count() > 0 ? device_sm_count() : 1;
+  const int64_t cap = (int64_t)sms * per_sm;
+  k_grad_f32_csr_staged<DIM><<<(int)(tiles < cap ? tiles : cap), kStageTile, 0, s>>>(a);
+  return true;
+}
+
 template <int DIM, int PL, typename CT, bool REC>
 static void grad_f32_ell_dispatch(const GradArgs& a, int grid, int block, cudaStream_t s) {
   if constexpr (REC) {
@@ -294,6 +421,9 @@ static void grad_f32_dispatch(bool coord64, const GradArgs& a, int grid, int blo
     else
       grad_f32_ell_dispatch<DIM, PL, float, false>(a, grid, block, s);
   } else if (rec) {
+    if constexpr (PL == PHI32PAIR) {
+      if (grad_f32_csr_staged<DIM>(a, s)) return;
+    }
     k_grad_f32<DIM, PL, float, true><<<grid, block, 0, s>>>(a);
   } else if (coord64) {
     k_grad_f32<DIM, PL, double, false><<<grid, block, 0, s>>>(a);

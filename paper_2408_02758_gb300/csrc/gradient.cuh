@@ -16,6 +16,7 @@ struct GradArgs {
   const void* coords;          // SoA [dim][n], float or double
   const int32_t* row_ptr;
   const int32_t* col_idx;
+  int64_t nnz;                 // entries of col_idx
   const void* phi;             // flowmap, layout per PhiLayout
   void* ftle_out;              // float [n] (double [n] when out64)
   double* lam_out;             // nullable

@@ -526,6 +526,65 @@ def test_abc_refresh_must_be_a_power_of_two(F):
         assert e.value.status == F.FTLE_EINVAL
 
 
+def _hub_mesh():
+    """A 128 x 64 triangle mesh whose node 0 also neighbours every other node (a row of 8191
+    entries, so the first tile's stretch of col_idx is longer than a stage holds)."""
+    m = I.make_mesh((128, 64), (0, 0), (2, 1), I.TRI, 0.3, 9)
+    n = m.n_nodes
+    rows = [set(m.col_idx[m.row_ptr[i]:m.row_ptr[i + 1]].tolist()) for i in range(n)]
+    rows[0] |= set(range(1, n))
+    for i in range(1, n):
+        rows[i].add(0)
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    ci = np.concatenate([np.array(sorted(r), np.int32) for r in rows])
+    return I.mesh_from_arrays(m.coords, rp, ci)
+
+
+@pytest.mark.parametrize("case", ["tri", "kuhn", "ragged", "hub", "offset"])
+def test_staged_csr_stretches_equal_direct_loads(F, case):
+    """The CSR gradient with each tile's stretch of col_idx staged in shared memory
+    (grad_staging = 0, the default) equals the plain-load kernel bit for bit: lattice meshes, a
+    ragged last tile, a hub row longer than a stage (read from global memory), and col_idx not
+    16-byte aligned (left to the plain kernel)."""
+    import torch
+
+    if case == "tri":
+        m = I.make_mesh((64, 48), (0, 0), (2, 1), I.TRI, 0.3, 5)
+    elif case == "kuhn":
+        m = I.make_mesh((24, 20, 18), (0, 0, 0), (2, 1, 1), I.KUHN, 0.3, 5)
+    elif case == "ragged":
+        m = I.make_mesh((17, 13, 11), (0, 0, 0), (2, 1, 1), I.KUHN, 0.3, 5)
+    else:
+        m = _hub_mesh()
+    dim = m.dim
+    flow = I.FlowSpec.double_gyre() if dim == 2 else I.FlowSpec.abc()
+    T = 3.0 if dim == 2 else 1.0
+    if case == "offset":
+        base = F.DeviceMesh.from_mesh(m)
+        ci = torch.empty(m.nnz + 1, dtype=torch.int32, device="cuda")
+        ci[1:] = base.col_idx
+        dm = F.DeviceMesh(base.coords, base.row_ptr, ci[1:])  # 4 bytes past a 256-byte boundary
+        assert dm.col_idx.data_ptr() % 16 == 4
+    else:
+        dm = F.DeviceMesh.from_mesh(m)
+    phi = F.flowmap_empty(dim, m.n_nodes, "fp32c")
+    F.ftle_advect(dm, flow, 0.0, T, 0.01, "fp32c", phi)
+    outs = []
+    for staging in (0, 1):
+        out = torch.full((m.n_nodes,), 9.0, device="cuda")
+        lam = torch.full((m.n_nodes,), 9.0, dtype=torch.float64, device="cuda")
+        ws = F.workspace_empty(F.ftle_workspace_bytes(m.n_nodes))
+        F.ftle_gradient_eig(dm, phi, "fp32c", T, out, lam, ws, options=F.make_options(grad_staging=staging))
+        cnt = F.ftle_read_counters(ws)
+        assert cnt["n_wait_timeouts"] == 0
+        outs.append((out.cpu(), lam.cpu(), cnt["n_flagged"]))
+    (a, la, fa), (b, lb, fb) = outs
+    assert fa == fb
+    assert torch.equal(torch.isnan(a), torch.isnan(b)) and torch.equal(a[~torch.isnan(a)], b[~torch.isnan(b)])
+    assert torch.equal(torch.isnan(la), torch.isnan(lb)) and torch.equal(la[~torch.isnan(la)], lb[~torch.isnan(lb)])
+
+
 def test_fixed_width_list_rejects_long_rows(F):
     w = I.preset(2, scale=1 / 32)
     dm = F.DeviceMesh.from_mesh(w.mesh)
