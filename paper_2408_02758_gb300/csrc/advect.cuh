@@ -347,9 +347,16 @@ __device__ __forceinline__ void rk4_step_c_full(const AdvArgs& a, const Coef& c0
 // first order (|d2 - d1| <= h^2/4 L U for a flow with Lipschitz constant L and speed bound U, so
 // the dropped (d2 - d1)^2 / 2 stays near float rounding: kTinyMax); stage four turns stage one's
 // by d3.  Without SAFE a stage angle beyond the turns' limits returns false (the caller then
-// evaluates the step in full).
-template <bool SAFE>
-__device__ __forceinline__ bool abc_step_from(const AdvArgs& a, const float* s0, const float* c0v, float* inc) {
+// evaluates the step in full).  With st4 (unchecked steps only) stage four's pairs and d3 are
+// handed back for the carried steps below.
+struct AbcStage4 {
+  float s[3], c[3], d3[3];
+};
+
+template <bool SAFE, bool KEEP4 = false>
+__device__ __forceinline__ bool abc_step_from(const AdvArgs& a, const float* s0, const float* c0v, float* inc,
+                                              AbcStage4* st4 = nullptr) {
+  static_assert(SAFE || !KEEP4, "stage four's pairs are kept by the unchecked step only");
   float d1[3], d2[3], d3[3], e4[3], mx = 0.0f;
   d1[0] = fmaf(a.habc[0][0], s0[2], a.habc[0][2] * c0v[1]);
   d1[1] = fmaf(a.habc[0][1], s0[0], a.habc[0][0] * c0v[2]);
@@ -370,7 +377,14 @@ __device__ __forceinline__ bool abc_step_from(const AdvArgs& a, const float* s0,
       mx = fmaxf(fmaxf(mx, fmaxf(fabsf(d1[0]), fmaxf(fabsf(d1[1]), fabsf(d1[2])))), dmax * (kRotMax / kTinyMax));
     abc_stage_k(a.habc[1], s3, c3, d3);
   }
-  abc_stage_rot<!SAFE>(a.habc[2], d3, s0, c0v, mx, e4);
+  if constexpr (KEEP4) {
+    rotate_small_xyz(s0, c0v, d3, st4->s, st4->c);
+    abc_stage_k(a.habc[2], st4->s, st4->c, e4);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) st4->d3[q] = d3[q];
+  } else {
+    abc_stage_rot<!SAFE>(a.habc[2], d3, s0, c0v, mx, e4);
+  }
   if (!(SAFE || mx <= kRotMax)) return false;
 #pragma unroll
   for (int q = 0; q < 3; ++q) inc[q] = fmaf(fmaf(2.f, d2[q], d1[q] + d3[q]), 1.0f / 3.0f, e4[q]);
@@ -379,21 +393,30 @@ __device__ __forceinline__ bool abc_step_from(const AdvArgs& a, const float* s0,
 
 // Stage one's (sin, cos) of the state carried from step to step by the unchecked compensated ABC
 // step (AdvArgs::rot_safe): a step whose index is a multiple of AdvArgs::abc_refresh evaluates
-// them afresh at the compensated state (fsincos_c); the steps between turn the previous step's
-// pairs by that step's increment (|inc| <= |h| U <= kRotMax, the same third-order turn as the
-// stages; the increment before its low part joins the state, which moves the angle by at most
-// half an ulp of the increment).  The turns' roundings accumulate over at most abc_refresh - 1
-// steps before the next fresh evaluation.
+// them afresh at the compensated state (fsincos_c); the steps between start from the previous
+// step's stage-four pairs, at x + d3 with d3 = h k3, and turn them to first order by what the
+// state moved beyond that point, inc - d3 = h/6 ((k1 - k3) + 2 (k2 - k3) + (k4 - k3)).  That
+// difference is third order in h (about h^3 L^2 U / 12; ~2e-6 rad at h = 0.01); in any case
+// |inc - d3| <= h^2 L U / 6 (1 + hL/2 + (hL)^2 / 8), below stage three's bound h^2 L U / 4
+// whenever hL <= kRotMax, so the host's kTinyMax check on stage three covers it and the dropped
+// (inc - d3)^2 / 2 stays below float rounding.  The increment is taken before its low part joins
+// the state, which moves the angle by at most half an ulp of the increment.  The turns'
+// roundings accumulate over at most abc_refresh - 1 steps before the next fresh evaluation.
 struct AbcCarry {
   float s[3], c[3];
 };
 
 // One carried step from the pairs in cy: the step's increment, the compensated state update,
-// and (with TURN) the pairs turned by the increment for the next step.
+// and (with TURN) the next step's pairs from stage four's, turned by inc - d3 (formed exactly
+// where inc and d3 agree within a factor of two, as they do unless both are tiny).
 template <bool TURN>
 __device__ __forceinline__ void abc_carried_one(const AdvArgs& a, float* xh, float* xl, AbcCarry& cy) {
   float inc[3];
-  abc_step_from<true>(a, cy.s, cy.c, inc);
+  AbcStage4 st4;
+  if constexpr (TURN)
+    abc_step_from<true, true>(a, cy.s, cy.c, inc, &st4);
+  else
+    abc_step_from<true>(a, cy.s, cy.c, inc);
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     float s, e;
@@ -401,7 +424,14 @@ __device__ __forceinline__ void abc_carried_one(const AdvArgs& a, float* xh, flo
     xh[q] = s;
     xl[q] = e;
   }
-  if constexpr (TURN) rotate_small_xyz(cy.s, cy.c, inc, cy.s, cy.c);
+  if constexpr (TURN) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float dl = inc[q] - st4.d3[q];
+      cy.s[q] = fmaf(st4.c[q], dl, st4.s[q]);
+      cy.c[q] = fmaf(-st4.s[q], dl, st4.c[q]);
+    }
+  }
 }
 
 __device__ __forceinline__ void abc_fresh_pairs(const float* xh, const float* xl, AbcCarry& cy) {
