@@ -106,6 +106,47 @@ def test_abc_bounds_hold_for_sampled_stage_increments(F, A, B, C, dt):
     assert worst_angle >= 0.5 * b["angle_bound"] and worst_diff >= 0.1 * b["diff_bound"], (worst_angle, worst_diff, b)
 
 
+def _abc_step_increment(A, B, C, h, p0):
+    """The RK4 increment h/6 (k1 + 2 k2 + 2 k3 + k4) of one ABC step and the stage-four increment
+    h k3."""
+
+    def vel(p):
+        x, y, z = p
+        return np.stack([A * np.sin(z) + C * np.cos(y), B * np.sin(x) + A * np.cos(z), C * np.sin(y) + B * np.cos(x)])
+
+    k1 = vel(p0)
+    k2 = vel(p0 + 0.5 * h * k1)
+    k3 = vel(p0 + 0.5 * h * k2)
+    k4 = vel(p0 + h * k3)
+    return h / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4), h * k3
+
+
+@pytest.mark.parametrize("A,B,C,dt", [
+    (math.sqrt(3.0), math.sqrt(2.0), 1.0, 0.01),
+    (1.0, 1.0, 1.0, 0.02),
+    (2.0, 0.5, 1.0, -0.005),
+])
+def test_abc_carried_turn_is_third_order_and_within_the_difference_bound(F, A, B, C, dt):
+    """A carried ABC step takes the next step's stage-one pairs from stage four's, turned to first
+    order by inc - h k3.  That angle is third order in h (its first- and second-order terms
+    cancel), bounded by h^2 L U / 6 (1 + hL/2 + (hL)^2 / 8) with L = U the largest pair sum, and
+    so stays within the stage-three difference bound the host already checks."""
+    b = F.ftle_rotation_bounds(I.FlowSpec.abc(A, B, C), abs(dt))
+    U = max(A + C, B + A, C + B)
+    h = abs(dt)
+    rng = np.random.default_rng(240802760)
+    p0 = rng.uniform(0.0, 2 * math.pi, (3, 400_000))
+    worst = []
+    for scale in (1.0, 0.5):
+        inc, d3 = _abc_step_increment(A, B, C, dt * scale, p0)
+        worst.append(np.abs(inc - d3).max())
+    hs = h
+    bound = hs * hs * U * U / 6.0 * (1.0 + hs * U / 2.0 + (hs * U) ** 2 / 8.0)
+    assert worst[0] <= bound <= b["diff_bound"], (worst, bound, b)
+    assert worst[0] / worst[1] > 7.0, worst  # third order: halving h divides it by ~8
+    assert worst[0] < 0.05 * b["diff_bound"], (worst, b)
+
+
 def test_unchecked_decision_and_validation(F):
     dg = F.ftle_rotation_bounds(I.FlowSpec.double_gyre(), 0.01)
     assert dg["unchecked"] and dg["angle_bound"] < dg["angle_limit"] and dg["diff_bound"] < dg["diff_limit"]
