@@ -603,7 +603,8 @@ def main():
         e2e = {"value": n / statistics.mean(te), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(oh.numel() * oh.element_size()),
                "ms_per_call": {"mean": 1e3 * statistics.mean(te), "median": 1e3 * statistics.median(te),
-                               "min": 1e3 * min(te), "max": 1e3 * max(te)}}
+                               "min": 1e3 * min(te), "max": 1e3 * max(te),
+                               "each": [round(1e3 * t, 3) for t in te]}}
         del hws
 
     if rank != 0:
