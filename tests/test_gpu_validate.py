@@ -131,3 +131,44 @@ def test_entry_points_refuse_bad_meshes_before_any_gather(F):
     assert torch.equal(torch.isnan(out), torch.isnan(ref)) and torch.equal(out[~torch.isnan(out)], ref[~torch.isnan(ref)])
     F.ftle_compute_host(ch, rp, torch.from_numpy(m.col_idx).pin_memory(), flow, 0.0, 2.0, 0.01, "fp32c", oh, hws)
     assert np.array_equal(oh.numpy(), ref.cpu().numpy(), equal_nan=True)
+
+
+@pytest.mark.parametrize("offset", [0, 1, 2, 3])
+def test_bad_entries_in_unaligned_heads_bodies_and_tails(F, offset):
+    """The pass reads the index lists as 16-byte vectors from their first 16-byte boundary and the
+    few entries before and after it one by one: lists starting 0-3 entries past a boundary, with
+    bad entries at the first entry, inside the vectors and at the last entry, are all found, and
+    the first position is reported relative to the list's own start."""
+    import torch
+
+    m = I.make_mesh((23, 17), (0, 0), (2, 1), I.TRI, 0.3, 43)
+    n, nnz = m.n_nodes, m.nnz
+    for where, values in (([0, 1, nnz // 2, nnz - 1], [n, -1, 2 ** 31 - 1, -5]),
+                          ([nnz - 1], [n]), ([nnz // 2 + 1], [-(2 ** 31)]), ([], [])):
+        ci = m.col_idx.copy()
+        for e, v in zip(where, values):
+            ci[e] = v
+        buf = torch.zeros(nnz + 4, dtype=torch.int32, device="cuda")
+        buf[offset:offset + nnz] = torch.from_numpy(ci).cuda()
+        dm = F.DeviceMesh(torch.from_numpy(np.ascontiguousarray(m.coords)).cuda(),
+                          torch.from_numpy(m.row_ptr).cuda(), buf[offset:offset + nnz])
+        assert (dm.col_idx.data_ptr() - buf.data_ptr()) == 4 * offset
+        rep = F.ftle_validate_mesh(dm, check=False)
+        assert rep["bad_col_idx"] == len(where), (offset, where, rep)
+        assert rep["first_bad_col"] == (min(where) if where else -1), (offset, where, rep)
+        assert rep["status"] == (F.FTLE_EINVAL if where else F.FTLE_OK)
+    # the fixed-width list: -1 is allowed, -2 and n are not; a list starting off a boundary
+    dm = _device(F, m)
+    dm.attach_ell()
+    w = dm.desc.ell_width
+    flat = dm.ell.reshape(-1).clone()
+    L = flat.numel()
+    bad = [0, L // 3, L - 1]
+    for e, v in zip(bad, [-2, n, -(2 ** 31)]):
+        flat[e] = v
+    buf = torch.zeros(L + 4, dtype=torch.int32, device="cuda")
+    buf[offset:offset + L] = flat
+    dm.ell = buf[offset:offset + L].view(w, n)
+    dm.desc.ell_idx = dm.ell.data_ptr()
+    rep = F.ftle_validate_mesh(dm, check=False)
+    assert rep["bad_ell_idx"] == 3 and rep["first_bad_ell"] == 0 and rep["bad_col_idx"] == 0, rep
