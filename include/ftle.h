@@ -165,16 +165,18 @@ typedef struct ftle_options {
                              when an index is out of range.  The check synchronises the stream
                              once per mesh (it reads its counters back), so it is off by default;
                              ftle_compute_host always runs it. */
-  int32_t grad_staging;   /* float gradient over the fixed-width list (compensated flowmaps,
-                             width 6 in 2D or 14 in 3D, n_nodes a multiple of 4, ell_idx 16-byte
-                             aligned): 0 stages each tile's index slices in shared memory by
-                             bulk copies (TMA) one tile ahead of the computation, 1 reads the
-                             indices with plain loads.  Same results either way. */
+  int32_t grad_staging;   /* float gradient of compensated flowmaps: 0 brings each tile's
+                             neighbour indices into shared memory by bulk copies (TMA) one tile
+                             ahead of the computation (the fixed-width list: width 6 in 2D or 14
+                             in 3D, n_nodes a multiple of 4, ell_idx 16-byte aligned; CSR rows:
+                             col_idx 16-byte aligned), 1 reads the indices with plain loads.
+                             Same results either way. */
   int32_t abc_refresh;    /* compensated ABC advection with the unchecked step (ftle_rotation_bounds
                              .unchecked): stage one's sines and cosines of the state are evaluated
-                             afresh every abc_refresh steps and, in between, carried from the
-                             previous step and turned by its increment (a power of two in
-                             [1, 1024]; default 8; 1 evaluates them at every step). */
+                             afresh every abc_refresh steps and, in between, taken from the
+                             previous step's stage four and turned by the rest of that step's
+                             increment (a power of two in [1, 1024]; default 8; 1 evaluates them
+                             at every step). */
 } ftle_options;
 
 /* ---------------------------------------------------------------------------------- sizes */
