@@ -469,8 +469,9 @@ def test_staged_index_tiles_equal_direct_loads(F, shape):
 
 @pytest.mark.parametrize("refresh", [1, 2, 8, 16])
 def test_abc_carried_stage_one_refresh(F, refresh):
-    """The compensated ABC step carries stage one's sines and cosines from step to step, turned by
-    each step's increment and evaluated afresh every abc_refresh steps: every period follows the
+    """The compensated ABC step carries stage one's sines and cosines from step to step (stage
+    four's pairs turned by the rest of the step's increment) and evaluates them afresh every
+    abc_refresh steps: every period follows the
     oracle at the parity tolerance (a ragged 500 steps against periods that do not divide it), and
     the batched kernel, carrying them the same way, gives the single kernel's flowmap bit for bit."""
     import torch
