@@ -19,6 +19,7 @@ Each step's kernels are bracketed by CUDA events on the launching stream; L2 is 
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -593,12 +594,17 @@ def main():
         for _ in range(2):
             ftle.ftle_compute_host(ch, rp, ci, w.flow, 0.0, w.T, w.dt, prec, oh, hws, options=hopt, stream=sh)
         te = []
-        for _ in range(args.e2e_steps):
-            flush.fill_(0.0)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ftle.ftle_compute_host(ch, rp, ci, w.flow, 0.0, w.T, w.dt, prec, oh, hws, options=hopt, stream=sh)
-            te.append(time.perf_counter() - t0)
+        gc.collect()
+        gc.disable()  # wall-clock timing: no collector pass inside a call (as timeit does)
+        try:
+            for _ in range(args.e2e_steps):
+                flush.fill_(0.0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ftle.ftle_compute_host(ch, rp, ci, w.flow, 0.0, w.T, w.dt, prec, oh, hws, options=hopt, stream=sh)
+                te.append(time.perf_counter() - t0)
+        finally:
+            gc.enable()
         h2d = ch.numel() * ch.element_size() + rp.numel() * 4 + ci.numel() * 4
         e2e = {"value": n / statistics.mean(te), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(oh.numel() * oh.element_size()),
