@@ -277,19 +277,6 @@ __device__ __forceinline__ void rotate_small_xyz(const float* s0, const float* c
   rotate_small(s0[2], c0[2], d[2], s[2], c[2]);
 }
 
-// The same three rotations with x and y as one paired f32x2 rotation (same bits).
-__device__ __forceinline__ void rotate_small_xyz_paired(const float* s0, const float* c0, const float* d, float* s,
-                                                        float* c) {
-  float2 sp, cp;
-  rotate_small2(make_float2(s0[0], s0[1]), make_float2(c0[0], c0[1]), make_float2(d[0], d[1]), sp, cp);
-  const float sz = s0[2], cz = c0[2];
-  s[0] = sp.x;
-  s[1] = sp.y;
-  c[0] = cp.x;
-  c[1] = cp.y;
-  rotate_small(sz, cz, d[2], s[2], c[2]);
-}
-
 // ABC stage two, three or four of the compensated step: stage one's (sin, cos) of x, y, z rotated
 // by the stage increments d (radians); with CHECK the largest increment joins `mx`.  co = (A, B, C) times
 // the scale of the value returned (the next stage's increment, or h/6 k4).

@@ -349,20 +349,6 @@ __device__ __forceinline__ void rotate_small2(float2 s0, float2 c0, float2 th, f
   c = fma2(c0, cm, fma2(neg2(s0), st, c0));
 }
 
-// --- double gyre, double precision
-__device__ __forceinline__ void dg_vel64(double A, double eps, double om, double t, double x,
-                                         double y, double& u, double& v) {
-  double s = sin(om * t);
-  double a = eps * s, b = 1.0 - 2.0 * eps * s;
-  double f = fma(a, x, b) * x;
-  double fx = fma(2.0 * a, x, b);
-  double sf, cf, sy, cy;
-  sincospi(f, &sf, &cf);
-  sincospi(y, &sy, &cy);
-  u = -kPi * A * sf * cy;
-  v = kPi * A * cf * sy * fx;
-}
-
 // --- ABC flow
 __device__ __forceinline__ void abc_vel32(float A, float B, float C, float x, float y, float z,
                                           float& u, float& v, float& w) {

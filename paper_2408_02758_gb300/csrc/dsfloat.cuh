@@ -75,9 +75,6 @@ __device__ __forceinline__ dsf ds_mul_f(dsf a, float b) {
   return ds_fast(p, e);
 }
 
-// a * b + c
-__device__ __forceinline__ dsf ds_fma(dsf a, dsf b, dsf c) { return ds_add(ds_mul(a, b), c); }
-
 __device__ __forceinline__ dsf ds_neg(dsf a) { return ds_make(-a.h, -a.l); }
 
 
