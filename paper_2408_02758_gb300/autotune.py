@@ -19,8 +19,8 @@ from pathlib import Path
 from typing import Callable, Iterable
 
 ADVECT_CANDIDATES = [(256, 32), (256, 8), (128, 16), (64, 32), (256, 4), (128, 64)]
-# gradient: the staged fixed-width-list kernel (fixed 256-thread tiles; the plain kernels where it
-# does not apply) or plain loads with 128 / 256 threads per block
+# gradient: the staged kernels (fixed-width list or CSR rows, fixed 256-thread tiles; the plain
+# kernels where they do not apply) or plain loads with 128 / 256 threads per block
 GRAD_CANDIDATES = [{"grad_staging": 0}, {"grad_block": 128, "grad_staging": 1}, {"grad_block": 256, "grad_staging": 1}]
 BATCH_TILE_CANDIDATES = [(256, 256), (128, 512), (256, 1024), (64, 256)]
 

@@ -29,8 +29,9 @@ struct GradArgs {
   const float4* rec;           // nullable: gradient records of a compensated flowmap (float coords)
   const int32_t* ell;          // nullable: fixed-width neighbour list [ell_width][n], -1 = none
   int ell_width;
-  bool staged;                 // fixed-width list: index tiles staged in shared memory by bulk
-                               // copies where the layout allows (k_grad_f32_ell_staged)
+  bool staged;                 // neighbour indices staged in shared memory by bulk copies where
+                               // the layout allows (k_grad_f32_ell_staged for the fixed-width
+                               // list, k_grad_f32_csr_staged for CSR rows)
   int stencil;                 // ftle_stencil: implicit lattice neighbours (0: from the lists)
   uint32_t grid[3];            // lattice nodes per axis when stencil != 0
   const int32_t* list;         // double kernel: nullable node list ...
