@@ -125,8 +125,6 @@ def params_for_compute(mesh, flow, T: float, dt: float, precision: str = "fp32c"
     ch = None if retune else cache.get(key)
     if ch is None:
         phi = ftle.flowmap_empty(mesh.dim, mesh.n_nodes, precision)
-        out = ftle.ftle_out_empty(mesh.n_nodes, precision)
-        ws = ftle.workspace_empty(ftle.ftle_workspace_bytes(mesh.n_nodes))
 
         def t_adv(c):
             o = ftle.make_options(advect_block=c["advect_block"], advect_blocks_per_sm=c["advect_blocks_per_sm"])
@@ -134,12 +132,35 @@ def params_for_compute(mesh, flow, T: float, dt: float, precision: str = "fp32c"
 
         adv = pick([{"advect_block": b, "advect_blocks_per_sm": s} for b, s in ADVECT_CANDIDATES], t_adv)
 
-        def t_grad(c):
-            o = ftle.make_options(**c)
-            return _event_timer(lambda: ftle.ftle_gradient_eig(mesh, phi, precision, T, out, None, ws, options=o))
-
-        gr = pick(GRAD_CANDIDATES, t_grad)
+        gr = _pick_gradient(mesh, phi, precision, T)  # phi: the last advection's flowmap
         ch = Choice({**adv.params, **gr.params}, adv.ms + gr.ms)
+        cache.put(key, ch)
+    return dict(ch.params)
+
+
+def _pick_gradient(mesh, phi, precision: str, T: float) -> Choice:
+    from . import ftle
+
+    out = ftle.ftle_out_empty(mesh.n_nodes, precision)
+    ws = ftle.workspace_empty(ftle.ftle_workspace_bytes(mesh.n_nodes))
+
+    def t_grad(c):
+        o = ftle.make_options(**c)
+        return _event_timer(lambda: ftle.ftle_gradient_eig(mesh, phi, precision, T, out, None, ws, options=o))
+
+    return pick(GRAD_CANDIDATES, t_grad)
+
+
+def params_for_gradient(mesh, phi, precision: str, T: float, cache: Cache | None = None,
+                        retune: bool = False) -> dict:
+    """The gradient launch shape (block, index staging) alone, for this mesh's neighbour layout,
+    timed on the flowmap phi; as ftle.make_options keyword arguments."""
+    cache = cache or Cache()
+    layout = "stencil" if mesh.desc.stencil else ("ell" if mesh.desc.ell_width else "csr")
+    key = shape_key(_gpu_name(), f"gradient-{layout}", mesh.dim, 0, precision, mesh.n_nodes, 1)
+    ch = None if retune else cache.get(key)
+    if ch is None:
+        ch = _pick_gradient(mesh, phi, precision, T)
         cache.put(key, ch)
     return dict(ch.params)
 

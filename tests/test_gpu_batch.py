@@ -109,6 +109,13 @@ def test_autotuned_options_give_identical_results(batch):
     a = ftle.compute(dm, w.flow, w.T, w.dt, "fp32c").cpu()
     b = ftle.compute(dm, w.flow, w.T, w.dt, "fp32c", options=opts).cpu()
     assert torch.equal(a, b)
+    # the gradient's shape alone, tuned on these CSR rows (the host-buffer path's layout)
+    phi = ftle.flowmap_empty(2, w.mesh.n_nodes, "fp32c")
+    ftle.ftle_advect(dm, w.flow, 0.0, w.T, w.dt, "fp32c", phi)
+    gp = autotune.params_for_gradient(dm, phi, "fp32c", w.T, cache=cache, retune=True)
+    assert set(gp) <= {"grad_block", "grad_staging"}
+    c = ftle.compute(dm, w.flow, w.T, w.dt, "fp32c", options=ftle.make_options(**gp)).cpu()
+    assert torch.equal(a, c)
     bopt = autotune.options_for_batch(meshes, [x.flow for x in ws_list], [x.T for x in ws_list], 0.01, "fp32c",
                                       cache=cache, retune=True)
     ws = ftle.workspace_empty(ftle.ftle_batch_workspace_bytes(meshes, "fp32c"))
