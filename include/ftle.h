@@ -152,7 +152,8 @@ typedef struct ftle_options {
   int32_t grad_block;     /* threads per block of the gradient kernel (multiple of 32) */
   int32_t grad_tile;      /* nodes per gradient tile (multiple of grad_block) */
   int32_t refine_lanes;   /* re-advection: active lanes per 32-thread block (1..32); fewer lanes
-                             spread a short node list over more SM sub-partitions */
+                             spread a short node list over more SM sub-partitions (the 3D ABC
+                             re-advection takes one warp per node and ignores it) */
   int32_t defer_fp64;     /* 1: ftle_gradient_eig leaves the flagged nodes' FP64 pass to the
                              ftle_refine that the caller runs next with these options, which
                              recomputes those nodes after the re-advection anyway (their outputs

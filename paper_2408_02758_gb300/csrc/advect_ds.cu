@@ -326,6 +326,160 @@ __global__ void __launch_bounds__(32) k_advect_ds_abc_tri(AdvArgs a) {
   }
 }
 
+// ------------------------------------------------------- run-parallel re-advection (3D ABC)
+//
+// One warp per node: lane 3j + d integrates coordinate d over run j of kAbcRuns runs of
+// L = ceil(nsteps / kAbcRuns) steps, with the three-lane float-float step above (lanes 30 and 31
+// integrate a dummy group).  The runs start from boundary states that lane 0 first computes with
+// the compensated float step (the main advection's, stage one carried where the host bounds the
+// angles; one lane, short dependent chains),
+// each run carries its RK4 tangent in float, and the runs are joined as the 2D gyre's are
+// (below): delta_0 = 0, delta_{j+1} = J_j delta_j + (F_j - x_{j+1}), x(T) = F_last + J_last
+// delta_last.  Lane d holds row d of its run's tangent.  The ABC Jacobian has a zero diagonal:
+// row d is (d u_d / d x_{d+1}, d u_d / d x_{d+2}) = (-Q_d sin x_{d+1}, P_d cos x_{d+2}) at the
+// columns d + 1 and d + 2, so a stage's tangent row takes the sine and cosine from the two partner
+// lanes and their rows of the stage matrix, all by shuffle.
+constexpr int kAbcRunWarps = 4;  // nodes per block
+
+// This lane's velocity component at y times a step fraction (as ds_tri_abc_vel), and this lane's
+// row of J(y) M for the stage matrix M whose rows the lanes hold (Pf, Qf: P_d, Q_d).
+__device__ __forceinline__ dsf ds_tri_abc_vel_tan(const DsTriConst& K, const dsf& y, const dsf& p, const dsf& q,
+                                                  float Pf, float Qf, const float* M, float* T) {
+  dsf sn, cs;
+  ds_sincos(y, sn, cs);
+  const dsf so = ds_make(__shfl_sync(0xffffffffu, sn.h, K.src_s), __shfl_sync(0xffffffffu, sn.l, K.src_s));
+  const dsf co = ds_make(__shfl_sync(0xffffffffu, cs.h, K.src_c), __shfl_sync(0xffffffffu, cs.l, K.src_c));
+  const float a1 = -Qf * __shfl_sync(0xffffffffu, sn.h, K.src_c);  // d u_d / d x_{d+1}
+  const float a2 = Pf * __shfl_sync(0xffffffffu, cs.h, K.src_s);   // d u_d / d x_{d+2}
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float m1 = __shfl_sync(0xffffffffu, M[c], K.src_c), m2 = __shfl_sync(0xffffffffu, M[c], K.src_s);
+    T[c] = fmaf(a1, m1, a2 * m2);
+  }
+  return ds_add(ds_mul_u(p, so), ds_mul_u(q, co));
+}
+
+// ds_tri_abc_step with this lane's tangent row carried along (RK4 of J' = grad(v) J, in float).
+__device__ __forceinline__ dsf ds_tri_abc_step_tan(const DsTriConst& K, const dsf& x, float* row, float Pf, float Qf,
+                                                   float h) {
+  float M[3], T1[3], T2[3], T3[3], T4[3];
+  const dsf d1 = ds_tri_abc_vel_tan(K, x, K.ph2, K.qh2, Pf, Qf, row, T1);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) M[c] = fmaf(0.5f * h, T1[c], row[c]);
+  const dsf d2 = ds_tri_abc_vel_tan(K, ds_add_u(x, d1), K.ph2, K.qh2, Pf, Qf, M, T2);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) M[c] = fmaf(0.5f * h, T2[c], row[c]);
+  const dsf d3 = ds_tri_abc_vel_tan(K, ds_add_u(x, d2), K.ph, K.qh, Pf, Qf, M, T3);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) M[c] = fmaf(h, T3[c], row[c]);
+  const dsf e4 = ds_tri_abc_vel_tan(K, ds_add_u(x, d3), K.ph6, K.qh6, Pf, Qf, M, T4);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) row[c] = fmaf(h * (1.0f / 6.0f), fmaf(2.0f, T2[c] + T3[c], T1[c] + T4[c]), row[c]);
+  const dsf sum = ds_add(ds_add(d1, d3), ds_make(2.0f * d2.h, 2.0f * d2.l));
+  return ds_add(x, ds_add(ds_mul(sum, K.third), e4));
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(32 * kAbcRunWarps) k_refine_runs_abc(AdvArgs a) {
+  __shared__ float2 s_bnd[kAbcRunWarps][kAbcRuns][3];  // boundary states (hi, lo) of runs 1 ..
+  const DsTriConst K = ds_tri_const(a);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int g = lane / 3;  // this lane's run; 10 for the idle lanes 30, 31
+  const bool run_lane = g < kAbcRuns;
+  const float Pf = (float)a.p[K.d], Qf = (float)a.p[(K.d + 2) % 3], hf = (float)a.h;
+  const int L = (a.nsteps + kAbcRuns - 1) / kAbcRuns;
+  const int64_t count = (int64_t)*a.list_count;
+  for (int64_t slot = (int64_t)blockIdx.x * kAbcRunWarps + wib; slot < count;
+       slot += (int64_t)gridDim.x * kAbcRunWarps) {  // the same slot on every lane of the warp
+    const int64_t i = (int64_t)a.list[slot];
+    if (lane == 0) {  // boundary states by the compensated float step
+      float xh[3], xl[3];
+      double xd[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        xd[q] = load_coord<CT>(a.coords, q * a.n_mesh + i);
+        xh[q] = (float)xd[q];
+        xl[q] = (float)(xd[q] - (double)xh[q]);
+      }
+      const Coef c0{0.f, 0.f, 0.f, 0.0};  // the ABC flow is autonomous
+      AbcCarry carry;  // the unchecked step carries stage one's pairs, as the main advection does
+      int k = 0;
+      for (int j = 1; j < kAbcRuns; ++j) {
+        const int kend = min(j * L, a.nsteps);
+        if (a.rot_safe)
+          abc_steps_carried(a, k, kend, xh, xl, carry);
+        else
+          for (; k < kend; ++k) rk4_step<FTLE_FLOW_ABC, 3, P32C, false>(a, c0, c0, c0, xh, xl, xd);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) s_bnd[wib][j][q] = make_float2(xh[q], xl[q]);
+      }
+    }
+    __syncwarp();
+    const double xd0 = load_coord<CT>(a.coords, K.d * a.n_mesh + i);
+    const float x0 = (float)xd0;
+    dsf x = ds_from_double(xd0);
+    if (run_lane && g > 0) {
+      const float2 b = s_bnd[wib][g][K.d];
+      x = ds_make(b.x, b.y);
+    }
+    float row[3] = {K.d == 0 ? 1.0f : 0.0f, K.d == 1 ? 1.0f : 0.0f, K.d == 2 ? 1.0f : 0.0f};
+    const int k0 = g * L;
+    for (int s = 0; s < L; ++s) {  // the same count on every lane; steps past nsteps are discarded
+      float rn[3] = {row[0], row[1], row[2]};
+      const dsf xn = ds_tri_abc_step_tan(K, x, rn, Pf, Qf, hf);
+      if (run_lane && k0 + s < a.nsteps) {
+        x = xn;
+        row[0] = rn[0];
+        row[1] = rn[1];
+        row[2] = rn[2];
+      }
+    }
+    // join: r_j = F_j - x_{j+1} on run j's lanes, delta carried through the runs on every lane
+    float r = 0.f;
+    if (run_lane && g < kAbcRuns - 1) {
+      const float2 b = s_bnd[wib][g + 1][K.d];
+      const dsf dr = ds_add(x, ds_neg(ds_make(b.x, b.y)));
+      r = dr.h + dr.l;
+    }
+    float dl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < kAbcRuns - 1; ++j) {
+      float nd[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int src = 3 * j + q;
+        const float f0 = __shfl_sync(0xffffffffu, row[0], src), f1 = __shfl_sync(0xffffffffu, row[1], src);
+        const float f2 = __shfl_sync(0xffffffffu, row[2], src), rq = __shfl_sync(0xffffffffu, r, src);
+        nd[q] = fmaf(f0, dl[0], fmaf(f1, dl[1], fmaf(f2, dl[2], rq)));
+      }
+      dl[0] = nd[0];
+      dl[1] = nd[1];
+      dl[2] = nd[2];
+    }
+    x = ds_add_f(x, fmaf(row[0], dl[0], fmaf(row[1], dl[1], row[2] * dl[2])));  // the last run's lanes
+    const float q0a = __shfl_sync(0xffffffffu, x0, lane + 1), q0b = __shfl_sync(0xffffffffu, x0, lane + 2);
+    const float qha = __shfl_sync(0xffffffffu, x.h, lane + 1), qhb = __shfl_sync(0xffffffffu, x.h, lane + 2);
+    const float qla = __shfl_sync(0xffffffffu, x.l, lane + 1), qlb = __shfl_sync(0xffffffffu, x.l, lane + 2);
+    if (g == kAbcRuns - 1) {
+      reinterpret_cast<float2*>(a.out)[K.d * a.n_mesh + i] = make_float2(x.h, x.l);
+      if (a.rec && K.d == 0) {
+        const float xs[3] = {x0, q0a, q0b}, ph[3] = {x.h, qha, qhb}, pl[3] = {x.l, qla, qlb};
+        store_record<3>(a.rec, i, xs, ph, pl);
+      }
+    }
+    __syncwarp();  // every lane has read the boundary states before lane 0 writes the next node's
+  }
+}
+
+int launch_refine_runs_abc(bool coord64, const AdvArgs& args, int grid, cudaStream_t s) {
+  if (coord64)
+    k_refine_runs_abc<double><<<grid, 32 * kAbcRunWarps, 0, s>>>(args);
+  else
+    k_refine_runs_abc<float><<<grid, 32 * kAbcRunWarps, 0, s>>>(args);
+  FTLE_LAUNCH_CHECK("k_refine_runs_abc launch");
+  return FTLE_OK;
+}
+
 // ------------------------------------------------------- run-parallel re-advection (2D gyre)
 //
 // The compensated advection leaves each node's (hi, lo) state at the boundaries of kSegments runs

@@ -378,6 +378,8 @@ int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
     a.seg_stride = (int64_t)(seg_slot_bytes(m->n_nodes) / sizeof(float2));
     a.seg_len = seg_len(nsteps);
     rc = launch_refine_runs_dg(m->coord_fp64 != 0, a, w + W.coef, sms * 8, s);
+  } else if (fl->kind == FTLE_FLOW_ABC && m->dim == 3 && nsteps >= kAbcRuns) {
+    rc = launch_refine_runs_abc(m->coord_fp64 != 0, a, sms * 8, s);  // runs of a node side by side
   } else {
     rc = launch_advect_ds(fl->kind, m->dim, m->coord_fp64 != 0, a, sms * 8, 32, s);
   }

@@ -53,6 +53,9 @@ int launch_advect_abc(int prec, int out, bool coord64, const AdvArgs& args, int 
 // Run-parallel float-float re-advection of a compensated 2D double-gyre flowmap (needs the run
 // boundary states, args.seg, and nsteps <= kSegMaxSteps); coef_ws: the workspace's table region.
 int launch_refine_runs_dg(bool coord64, const AdvArgs& args, void* coef_ws, int grid, cudaStream_t s);
+// 3D ABC re-advection in kAbcRuns runs per node side by side (nsteps >= kAbcRuns).
+constexpr int kAbcRuns = 10;
+int launch_refine_runs_abc(bool coord64, const AdvArgs& args, int grid, cudaStream_t s);
 int launch_advect_ds(int kind, int dim, bool coord64, const AdvArgs& args, int grid, int block,
                      cudaStream_t stream);
 int launch_advect_misc(int kind, int dim, int prec, int out, bool coord64, const AdvArgs& args,

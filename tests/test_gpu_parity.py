@@ -400,6 +400,30 @@ def test_run_parallel_readvection_matches_fp64_flowmap(F, T):
     assert err < 1e-10, err
 
 
+@pytest.mark.parametrize("T", [5.0, 1.23, 0.17, -2.0, 0.05])
+def test_run_parallel_abc_readvection_matches_fp64_flowmap(F, T):
+    """The 3D ABC re-advection integrates a node's runs side by side (ten runs, three lanes each,
+    boundary states from the compensated float step, joined through each run's tangent): the
+    re-advected flowmap agrees with the FP64 oracle at float-float accuracy for the workload's 500
+    steps, step counts that do not divide into the runs (123), runs of two steps with the last
+    ones empty (17), a backward horizon, and fewer steps than runs (5: the one-run kernel)."""
+    w = I.preset(2, scale=1 / 16)  # 16^3 jittered Kuhn mesh
+    dm = F.DeviceMesh.from_mesh(w.mesh)
+    opt = F.make_options(refine_kappa=0.3)  # a wide re-advection list
+    out = F.compute(dm, w.flow, T, w.dt, "fp32c", return_all=True, options=opt)
+    cnt = F.ftle_read_counters(out["workspace"])
+    n = w.mesh.n_nodes
+    assert cnt["n_readvected"] > 0
+    off = 256 + ((4 * n + 255) // 256) * 256
+    ws = out["workspace"].cpu().numpy()
+    marked = np.frombuffer(ws[off: off + 4 * cnt["n_readvected"]].tobytes(), dtype=np.int32)
+    ph = F.flowmap_pairs(out["phi"], 3, n).double().cpu().numpy()
+    ph = ph[..., 0] + ph[..., 1]
+    ref = O.advect(w.flow.kind, w.flow.params, w.mesh.coords[:, marked], T, w.dt)
+    err = np.abs(ph[:, marked] - ref).max()
+    assert err < 1e-10, (err, len(marked))
+
+
 @pytest.mark.parametrize("preset,scale,kappa", [(1, 1 / 16, 0.01), (2, 1 / 8, 0.3)])
 def test_readvection_independent_of_lanes_per_block(F, preset, scale, kappa):
     """How many nodes a block of the float-float re-advection takes (refine_lanes; the 2D double
