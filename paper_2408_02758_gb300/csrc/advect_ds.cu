@@ -332,10 +332,11 @@ __global__ void __launch_bounds__(32) k_advect_ds_abc_tri(AdvArgs a) {
 // L = ceil(nsteps / kAbcRuns) steps, with the three-lane float-float step above (lanes 30 and 31
 // integrate a dummy group).  The runs start from boundary states that lane 0 first computes with
 // the compensated float step (the main advection's, stage one carried where the host bounds the
-// angles; one lane, short dependent chains),
-// each run carries its RK4 tangent in float, and the runs are joined as the 2D gyre's are
-// (below): delta_0 = 0, delta_{j+1} = J_j delta_j + (F_j - x_{j+1}), x(T) = F_last + J_last
-// delta_last.  Lane d holds row d of its run's tangent.  The ABC Jacobian has a zero diagonal:
+// angles; one lane, short dependent chains), each run carries its RK4 tangent in float, and the
+// runs are joined as the 2D gyre's are (below): delta_0 = 0, delta_{j+1} = J_j delta_j + (F_j -
+// x_{j+1}), x(T) = F_last + J_last delta_last.  At 256^3 (803 nodes, 500 steps) the boundary pass
+// takes ~0.07 ms and the runs ~0.06 ms, against 0.36 ms for all 500 steps on one lane group.
+// Lane d holds row d of its run's tangent.  The ABC Jacobian has a zero diagonal:
 // row d is (d u_d / d x_{d+1}, d u_d / d x_{d+2}) = (-Q_d sin x_{d+1}, P_d cos x_{d+2}) at the
 // columns d + 1 and d + 2, so a stage's tangent row takes the sine and cosine from the two partner
 // lanes and their rows of the stage matrix, all by shuffle.
