@@ -400,17 +400,21 @@ def test_run_parallel_readvection_matches_fp64_flowmap(F, T):
     assert err < 1e-10, err
 
 
-@pytest.mark.parametrize("T", [5.0, 1.23, 0.17, -2.0, 0.05])
-def test_run_parallel_abc_readvection_matches_fp64_flowmap(F, T):
+@pytest.mark.parametrize("T,dt", [(5.0, 0.01), (1.23, 0.01), (0.17, 0.01), (-2.0, 0.01), (0.05, 0.01), (1.0, 0.02)])
+def test_run_parallel_abc_readvection_matches_fp64_flowmap(F, T, dt):
     """The 3D ABC re-advection integrates a node's runs side by side (ten runs, three lanes each,
     boundary states from the compensated float step, joined through each run's tangent): the
     re-advected flowmap agrees with the FP64 oracle at float-float accuracy for the workload's 500
     steps, step counts that do not divide into the runs (123), runs of two steps with the last
-    ones empty (17), a backward horizon, and fewer steps than runs (5: the one-run kernel)."""
+    ones empty (17), a backward horizon, fewer steps than runs (5: the one-run kernel), and steps
+    long enough that the boundary pass takes the checked step (dt = 0.02: angles past the
+    unchecked turns' limit)."""
     w = I.preset(2, scale=1 / 16)  # 16^3 jittered Kuhn mesh
     dm = F.DeviceMesh.from_mesh(w.mesh)
     opt = F.make_options(refine_kappa=0.3)  # a wide re-advection list
-    out = F.compute(dm, w.flow, T, w.dt, "fp32c", return_all=True, options=opt)
+    if dt != 0.01:
+        assert not F.ftle_rotation_bounds(w.flow, dt)["unchecked"]
+    out = F.compute(dm, w.flow, T, dt, "fp32c", return_all=True, options=opt)
     cnt = F.ftle_read_counters(out["workspace"])
     n = w.mesh.n_nodes
     assert cnt["n_readvected"] > 0
@@ -419,7 +423,7 @@ def test_run_parallel_abc_readvection_matches_fp64_flowmap(F, T):
     marked = np.frombuffer(ws[off: off + 4 * cnt["n_readvected"]].tobytes(), dtype=np.int32)
     ph = F.flowmap_pairs(out["phi"], 3, n).double().cpu().numpy()
     ph = ph[..., 0] + ph[..., 1]
-    ref = O.advect(w.flow.kind, w.flow.params, w.mesh.coords[:, marked], T, w.dt)
+    ref = O.advect(w.flow.kind, w.flow.params, w.mesh.coords[:, marked], T, dt)
     err = np.abs(ph[:, marked] - ref).max()
     assert err < 1e-10, (err, len(marked))
 
