@@ -48,11 +48,12 @@ FLUSH_BYTES = 320 << 20
 #   ABC:         stage one 87 when evaluated afresh (three compensated sincos 78, increments 9)
 #                or 24 when carried from the previous step (stage four's three pairs turned to
 #                first order by the rest of the step's increment 15, increments 9; fresh once
-#                every abc_refresh = 8 steps), stages two and four 2 x 54 (three rotations 45,
-#                increments 9), stage three 24 (three first-order turns 15, increments 9),
+#                every abc_refresh = 8 steps), stage two 48 (three rotations without the
+#                fourth-order cosine term 39, increments 9), stage three 24 (three first-order
+#                turns 15, increments 9), stage four 54 (three rotations 45, increments 9),
 #                update 27
 ABC_REFRESH = 8
-FLOPS_PER_POINT_STEP = {"dg": 215, "abc": 246 - 63 * (ABC_REFRESH - 1) / ABC_REFRESH}
+FLOPS_PER_POINT_STEP = {"dg": 215, "abc": 240 - 63 * (ABC_REFRESH - 1) / ABC_REFRESH}
 
 
 def peak_fp32_tflops(sms: int, mhz: float) -> float:
