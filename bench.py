@@ -41,10 +41,11 @@ FLUSH_BYTES = 320 << 20
 # flops; one sincospi or sincos counted as 20 flops: argument reduction plus degree-7/8 minimax
 # polynomials; a small-angle rotation of a (sin, cos) pair 15).
 #   double gyre: stage one 74 (error-free f 17, two sincospi 40, first-order corrections 10,
-#                slope and velocity 7), per-step terms 6, stages two and four 2 x 43 (two
-#                rotations 30, angles 7, slope 2, increment 1, velocity 3), stage three 27
-#                (angles and their differences 11, four first-order turns 12, slope and
-#                velocity 4), update 22 (the step scale in two parts)
+#                slope and velocity 7), per-step terms 6, stage two 39 (two rotations without
+#                the fourth-order cosine term 26, angles 7, slope 2, increment 1, velocity 3),
+#                stage four 43 (two rotations 30, the same 13), stage three 27 (angles and
+#                their differences 11, four first-order turns 12, slope and velocity 4), update
+#                22 (the step scale in two parts)
 #   ABC:         stage one 87 when evaluated afresh (three compensated sincos 78, increments 9)
 #                or 24 when carried from the previous step (stage four's three pairs turned to
 #                first order by the rest of the step's increment 15, increments 9; fresh once
@@ -53,7 +54,7 @@ FLUSH_BYTES = 320 << 20
 #                turns 15, increments 9), stage four 54 (three rotations 45, increments 9),
 #                update 27
 ABC_REFRESH = 8
-FLOPS_PER_POINT_STEP = {"dg": 215, "abc": 240 - 63 * (ABC_REFRESH - 1) / ABC_REFRESH}
+FLOPS_PER_POINT_STEP = {"dg": 211, "abc": 240 - 63 * (ABC_REFRESH - 1) / ABC_REFRESH}
 
 
 def peak_fp32_tflops(sms: int, mhz: float) -> float:
