@@ -366,6 +366,7 @@ int ftle_backward(const ftle_mesh* mesh, const ftle_flow* flow, double t0, doubl
                   const void* flowmap, const void* checkpoints, int32_t ckpt_every, const float* dL_dftle,
                   double* dL_dparams, void* workspace, size_t workspace_bytes, const ftle_options* opt,
                   void* stream) {
+  PhaseRange range("ftle.backward");
   int rc, nsteps = 0;
   if ((rc = check_mesh(mesh)) || (rc = check_flow(flow, mesh->dim)) || (rc = check_prec(precision)) ||
       (rc = check_time(T, dt, &nsteps)))

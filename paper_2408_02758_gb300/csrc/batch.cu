@@ -474,6 +474,7 @@ size_t ftle_batch_workspace_bytes(int32_t n_inst, const ftle_mesh* meshes, int32
 int ftle_batch(int32_t n_inst, const ftle_mesh* meshes, const ftle_flow* flows, const double* T, double dt,
                int32_t precision, void* const* ftle_out, void* workspace, size_t workspace_bytes,
                const ftle_options* opt, void* stream) {
+  PhaseRange range("ftle.batch");
   BatchPlanHost P;
   int rc = plan_batch(n_inst, meshes, flows, T, dt, precision, ftle_out, workspace, workspace_bytes, opt, P);
   if (rc) return rc;
@@ -533,6 +534,7 @@ int ftle_batch_plan_create(int32_t n_inst, const ftle_mesh* meshes, const ftle_f
 
 int ftle_batch_plan_launch(ftle_batch_plan* plan, void* stream) {
   if (!plan || !plan->exec) return fail(FTLE_EINVAL, "plan is NULL or not instantiated");
+  PhaseRange range("ftle.batch_plan_launch");
   FTLE_CUDA_CHECK(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
   return FTLE_OK;
 }

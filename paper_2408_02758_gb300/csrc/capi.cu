@@ -332,6 +332,7 @@ bool refine_runs(const ftle_mesh* m, int precision, const Launch& L) {
 int run_gradient(const ftle_mesh* m, const void* phi, int precision, double T, void* ftle_out,
                  double* lam_out, void* ws, const Launch& L, cudaStream_t s, bool fixup) {
   if (m->n_nodes == 0) return FTLE_OK;
+  PhaseRange range("ftle.gradient");
   GradArgs g = make_grad_args(m, phi, T, ftle_out, lam_out, ws, L);
   g.rec = rec_ptr(m, phi, precision);
   const int sms = device_sm_count() > 0 ? device_sm_count() : 1;
@@ -353,6 +354,7 @@ int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
                int precision, void* phi, void* ftle_out, double* lam_out, void* ws, const Launch& L,
                cudaStream_t s) {
   if (!refine_runs(m, precision, L)) return FTLE_OK;
+  PhaseRange range("ftle.refine");
   const WsLayout W = ws_layout(m->n_nodes);
   char* w = reinterpret_cast<char*>(ws);
   ftle_counters* hdr = reinterpret_cast<ftle_counters*>(w + W.header);
@@ -390,6 +392,7 @@ int run_refine(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
 int run_advect(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, double dt, int nsteps,
                int precision, void* phi, void* ckpt, int ckpt_every, const Launch& L, cudaStream_t s) {
   if (m->n_nodes == 0) return FTLE_OK;
+  PhaseRange range("ftle.advect");
   AdvArgs a = make_adv_args(m, fl, t0, T, dt, nsteps);
   a.abc_refresh = L.abc_refresh;
   a.out = phi;
@@ -648,6 +651,7 @@ int ftle_compute_host(int32_t dim, int64_t n_nodes, int64_t nnz, const void* coo
   if (out_view) ftle_dev = out_view;
   // The neighbour lists are needed only once the flowmap is done, so they cross on a side stream
   // while the advection (which needs the coordinates alone) runs.
+  PhaseRange range("ftle.compute_host");
   SideStream side;
   if ((rc = side.open(s))) return rc;
   if (n_nodes > 0) {

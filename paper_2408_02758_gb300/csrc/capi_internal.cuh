@@ -1,11 +1,24 @@
 // Internal helpers shared by the C-ABI translation units (capi.cu, batch.cu, adjoint.cu).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "advect.cuh"
 #include "common.cuh"
 #include "gradient.cuh"
 
 namespace ftle {
+
+// A named range on the host timeline around one phase of a call (advection, gradient, the
+// re-advection, the list copies and checks, a batch, the adjoint), for profilers that record
+// NVTX ranges (e.g. ncu --nvtx --nvtx-include "ftle.gradient/"); without one attached the calls
+// do nothing.  Header-only NVTX 3: no library to link.
+struct PhaseRange {
+  explicit PhaseRange(const char* name) { nvtxRangePushA(name); }
+  ~PhaseRange() { nvtxRangePop(); }
+  PhaseRange(const PhaseRange&) = delete;
+  PhaseRange& operator=(const PhaseRange&) = delete;
+};
 
 struct Launch {
   double refine_kappa = 4e-4;

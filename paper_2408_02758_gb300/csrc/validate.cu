@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(kValBlock, kValBlocksPerSm)
 }
 
 int launch_validate_mesh(const ftle_mesh* m, MeshCheck* dev_out, cudaStream_t s) {
+  PhaseRange range("ftle.validate_mesh");
   const int64_t n = m->n_nodes;
   FTLE_CUDA_CHECK(cudaMemsetAsync(dev_out->count, 0, sizeof dev_out->count, s));
   FTLE_CUDA_CHECK(cudaMemsetAsync(dev_out->first, 0xFF, sizeof dev_out->first, s));
