@@ -463,7 +463,7 @@ def main():
                     help="preset index: 0 structured 2D, 1 triangle 2D, 2 tet 3D (default), 3 batched, "
                          "4 differentiable")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--csr", action="store_true",
                     help="gradient over the CSR rows instead of the fixed-width neighbour list")
     ap.add_argument("--stencil", action="store_true",
