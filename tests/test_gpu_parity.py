@@ -521,6 +521,24 @@ def test_abc_carried_stage_one_refresh(F, refresh):
     assert torch.equal(torch.isnan(a), torch.isnan(b)) and torch.equal(a[~torch.isnan(a)], b[~torch.isnan(b)])
 
 
+@pytest.mark.parametrize("A,B,C,dt,T", [(1.0, 1.0, 1.0, 0.005, 3.0), (2.0, 0.5, 1.0, 0.01, 2.0),
+                                         (math.sqrt(3.0), math.sqrt(2.0), 1.0, 0.011, 5.06)])
+def test_abc_unchecked_step_other_parameters(F, A, B, C, dt, T):
+    """The unchecked compensated ABC step (stage one carried from stage four, stage two's shorter
+    turn) on other flow parameters and step sizes, each within the host's bounds for the
+    unchecked step: the whole field of a 24^3 Kuhn mesh follows the oracle at the parity
+    tolerance."""
+    flow = I.FlowSpec.abc(A, B, C)
+    assert F.ftle_rotation_bounds(flow, dt)["unchecked"]
+    w = I.preset(2, scale=3 / 32)  # 24^3 jittered Kuhn mesh
+    ft, lam, _, cnt = run_gpu(F, w.mesh, flow, T, dt, "fp32c")
+    o = _oracle_full(w.mesh, flow, T, dt)
+    rep = compare(ft, o["ftle"], o["lam"])
+    report(w.name, rep, sample="every node", precision="fp32c", A=A, B=B, C=C, dt=dt, T=T)
+    assert rep["ok"], rep
+    assert cnt["n_degenerate"] == 0
+
+
 @pytest.mark.parametrize("T", [5.0, 2.47, 23.0])
 def test_abc_carried_steps_with_and_without_checkpoints(F, T):
     """The carried ABC steps run grouped between refreshes (a whole group of the default period
