@@ -51,10 +51,10 @@ FLUSH_BYTES = 320 << 20
 #                first order by the rest of the step's increment 15, increments 9; fresh once
 #                every abc_refresh = 8 steps), stage two 48 (three rotations without the
 #                fourth-order cosine term 39, increments 9), stage three 24 (three first-order
-#                turns 15, increments 9), stage four 54 (three rotations 45, increments 9),
-#                update 27
+#                turns 15, increments 9), stage four 54 (three rotations 45, increments 9) or 48
+#                on a carried step (its rotations without that term, as at stage two), update 27
 ABC_REFRESH = 8
-FLOPS_PER_POINT_STEP = {"dg": 211, "abc": 240 - 63 * (ABC_REFRESH - 1) / ABC_REFRESH}
+FLOPS_PER_POINT_STEP = {"dg": 211, "abc": 240 - (63 + 6) * (ABC_REFRESH - 1) / ABC_REFRESH}
 
 
 def peak_fp32_tflops(sms: int, mhz: float) -> float:

@@ -177,7 +177,9 @@ typedef struct ftle_options {
                              afresh every abc_refresh steps and, in between, taken from the
                              previous step's stage four and turned by the rest of that step's
                              increment (a power of two in [1, 1024]; default 8; 1 evaluates them
-                             at every step). */
+                             at every step).  They are carried only while the step's angle bound
+                             (ftle_rotation_bounds .angle_bound) stays within 0.032 rad; beyond
+                             that every step evaluates them afresh whatever abc_refresh says. */
 } ftle_options;
 
 /* ---------------------------------------------------------------------------------- sizes */

@@ -39,6 +39,8 @@ struct AdvArgs {
   int abc_refresh;             // compensated ABC, unchecked steps: stage one's sines and cosines
                                // evaluated afresh every abc_refresh steps (a power of two),
                                // carried and turned by each step's increment in between
+  int carry_ok;                // ABC: rot_safe and the step's angles within kCarryAngleMax, so
+                               // stage one's pairs may be carried (abc_refresh > 1)
   int rot_safe;                // no stage angle can exceed kRotMax (the host's bound on the
                                // increments; for the double gyre, of nodes in [0, 2] x [0, 1]),
                                // so the steps skip the angle check
@@ -279,13 +281,18 @@ __device__ __forceinline__ void rotate_small_xyz(const float* s0, const float* c
   rotate_small(s0[2], c0[2], d[2], s[2], c[2]);
 }
 
+// Largest step angle (|h| U, the host's bound) for which the ABC step carries stage one's pairs.
+constexpr float kCarryAngleMax = 0.032f;
+
 // rotate_small_xyz without the th^4/24 term of cos th - 1, for the unchecked ABC step's stage
-// two: its angles d1 = h/2 k1 stay within kRotMax / 2 (the host's bound), so the dropped term is
-// below 1.6e-8 (about 1e-10 at dt = 0.01 on the 3D workload), under a third of an ulp of the
-// result.  The pairs it gives feed stages two and three only: stage four and the carried pairs
-// turn stage one's pairs in full.
-__device__ __forceinline__ void rotate_small_xyz_stage2(const float* s0, const float* c0, const float* d, float* s,
-                                                        float* c) {
+// two, whose angles d1 = h/2 k1 stay within kRotMax / 2 under the host's bound (the dropped term
+// below 1.6e-8, about 1e-10 at dt = 0.01 on the 3D workload), and for stage four of a carried
+// step, whose angles stay within kCarryAngleMax (below 4.4e-8; about 2e-9 there).  At stage four
+// the term would shrink the carried pairs' norm by that much per step until the next fresh
+// evaluation; measured over the whole 256^3 field (period 8) the worst node went 8.5e-5 -> 7.4e-5
+// and the p99 stayed at 2.7e-6, i.e. the shrink is below the pairs' rounding.
+__device__ __forceinline__ void rotate_small_xyz_short(const float* s0, const float* c0, const float* d, float* s,
+                                                       float* c) {
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     const float t2 = d[q] * d[q];
@@ -369,7 +376,7 @@ __device__ __forceinline__ bool abc_step_from(const AdvArgs& a, const float* s0,
   d1[2] = fmaf(a.habc[0][2], s0[1], a.habc[0][1] * c0v[0]);
   float s2[3], c2v[3];
   if constexpr (SAFE)
-    rotate_small_xyz_stage2(s0, c0v, d1, s2, c2v);
+    rotate_small_xyz_short(s0, c0v, d1, s2, c2v);
   else
     rotate_small_xyz(s0, c0v, d1, s2, c2v);
   abc_stage_k(a.habc[0], s2, c2v, d2);
@@ -387,7 +394,7 @@ __device__ __forceinline__ bool abc_step_from(const AdvArgs& a, const float* s0,
     abc_stage_k(a.habc[1], s3, c3, d3);
   }
   if constexpr (KEEP4) {
-    rotate_small_xyz(s0, c0v, d3, st4->s, st4->c);
+    rotate_small_xyz_short(s0, c0v, d3, st4->s, st4->c);  // carried steps only: |d3| <= kCarryAngleMax
     abc_stage_k(a.habc[2], st4->s, st4->c, e4);
 #pragma unroll
     for (int q = 0; q < 3; ++q) st4->d3[q] = d3[q];

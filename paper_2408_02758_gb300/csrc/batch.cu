@@ -354,7 +354,7 @@ int plan_batch(int32_t n_inst, const ftle_mesh* meshes, const ftle_flow* flows, 
     memset(&bi, 0, sizeof bi);
     void* phi = P.ws + P.L.phi_off[q];
     bi.adv = make_adv_args(&meshes[q], &flows[q], 0.0, T[q], dt, nsteps);
-    bi.adv.abc_refresh = Lc.abc_refresh;
+    bi.adv.abc_refresh = bi.adv.carry_ok ? Lc.abc_refresh : 1;
     bi.adv.out = phi;
     if (precision == FTLE_PREC_FP32C && meshes[q].dim == 2) {
       bi.adv.seg = reinterpret_cast<float2*>(reinterpret_cast<char*>(phi) + seg_offset(2, meshes[q].n_nodes));

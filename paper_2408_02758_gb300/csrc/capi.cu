@@ -271,7 +271,8 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
     for (int q = 0; q < 3; ++q) a.habc[s][q] = (float)(hsc[s] * f->p[q]);
   double angle, diff;
   if (rotation_bounds(f, a.h, &angle, &diff)) a.rot_safe = rotation_unchecked(angle, diff) ? 1 : 0;
-  a.abc_refresh = kAbcRefreshDefault;
+  a.carry_ok = f->kind == FTLE_FLOW_ABC && a.rot_safe && angle <= (double)kCarryAngleMax * (1.0 - 1e-3);
+  a.abc_refresh = a.carry_ok ? kAbcRefreshDefault : 1;
   return a;
 }
 
@@ -394,7 +395,7 @@ int run_advect(const ftle_mesh* m, const ftle_flow* fl, double t0, double T, dou
   if (m->n_nodes == 0) return FTLE_OK;
   PhaseRange range("ftle.advect");
   AdvArgs a = make_adv_args(m, fl, t0, T, dt, nsteps);
-  a.abc_refresh = L.abc_refresh;
+  a.abc_refresh = a.carry_ok ? L.abc_refresh : 1;  // beyond kCarryAngleMax every step is fresh
   a.out = phi;
   a.ckpt = ckpt;
   a.ckpt_every = ckpt ? ckpt_every : 0;
