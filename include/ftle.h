@@ -225,13 +225,16 @@ int ftle_advect(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double 
  *   angle_bound  bound on every stage angle, radians (double gyre: the larger of pi f's and pi y's);
  *   diff_bound   bound on stage three's angle differences;
  *   angle_limit, diff_limit  the limits with their 1e-3 margin (0.05 and 3e-4 before it);
- *   unchecked    1 when both bounds are within their limits, else 0.
+ *   unchecked    1 when both bounds are within their limits, else 0;
+ *   carried      ABC: 1 when the unchecked step also carries stage one's sines and cosines from
+ *                step to step (ftle_options.abc_refresh > 1 asks for it), i.e. unchecked and
+ *                angle_bound within 0.032 rad (with the same margin); else 0.
  * Flows without the rotated step (linear, saddle): unchecked = 0, both bounds +inf.
  * Host only (no device work).  Errors: FTLE_EINVAL (null flow or out, unknown kind, parameters
  * or dt not finite, dt = 0). */
 typedef struct {
   int32_t unchecked;
-  int32_t reserved;
+  int32_t carried;
   double angle_bound;
   double diff_bound;
   double angle_limit;

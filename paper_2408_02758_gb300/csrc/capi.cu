@@ -240,6 +240,12 @@ static bool rotation_unchecked(double angle, double diff) {
   return angle <= (double)kRotMax * (1.0 - 1e-3) && diff <= (double)kTinyMax * (1.0 - 1e-3);
 }
 
+// The ABC step carries stage one's pairs (abc_refresh > 1) only while the step's angle bound stays
+// within kCarryAngleMax, where its shorter stage-four turn drops less than 4.4e-8.
+static bool carry_allowed(const ftle_flow* f, bool unchecked, double angle) {
+  return f->kind == FTLE_FLOW_ABC && unchecked && angle <= (double)kCarryAngleMax * (1.0 - 1e-3);
+}
+
 AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double T, double dt, int nsteps) {
   AdvArgs a;
   memset(&a, 0, sizeof a);
@@ -271,7 +277,7 @@ AdvArgs make_adv_args(const ftle_mesh* m, const ftle_flow* f, double t0, double 
     for (int q = 0; q < 3; ++q) a.habc[s][q] = (float)(hsc[s] * f->p[q]);
   double angle, diff;
   if (rotation_bounds(f, a.h, &angle, &diff)) a.rot_safe = rotation_unchecked(angle, diff) ? 1 : 0;
-  a.carry_ok = f->kind == FTLE_FLOW_ABC && a.rot_safe && angle <= (double)kCarryAngleMax * (1.0 - 1e-3);
+  a.carry_ok = carry_allowed(f, a.rot_safe != 0, angle);
   a.abc_refresh = a.carry_ok ? kAbcRefreshDefault : 1;
   return a;
 }
@@ -488,7 +494,7 @@ int ftle_rotation_bounds(const ftle_flow* flow, double dt, ftle_rotation_info* o
   double angle, diff;
   const bool rotated = rotation_bounds(flow, dt, &angle, &diff);
   out->unchecked = rotated && rotation_unchecked(angle, diff) ? 1 : 0;
-  out->reserved = 0;
+  out->carried = carry_allowed(flow, out->unchecked != 0, angle) ? 1 : 0;
   out->angle_bound = angle;
   out->diff_bound = diff;
   out->angle_limit = (double)kRotMax * (1.0 - 1e-3);

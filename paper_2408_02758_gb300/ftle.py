@@ -41,7 +41,7 @@ class ftle_counters(Structure):
 
 
 class ftle_rotation_info(Structure):
-    _fields_ = [("unchecked", c_int32), ("reserved", c_int32), ("angle_bound", c_double), ("diff_bound", c_double),
+    _fields_ = [("unchecked", c_int32), ("carried", c_int32), ("angle_bound", c_double), ("diff_bound", c_double),
                 ("angle_limit", c_double), ("diff_limit", c_double)]
 
 
@@ -269,8 +269,8 @@ def ftle_rotation_bounds(flow, dt: float) -> dict:
     f = make_flow(flow)
     info = ftle_rotation_info()
     _check("ftle_rotation_bounds", lib().ftle_rotation_bounds(ctypes.byref(f), dt, ctypes.byref(info)))
-    return {"unchecked": bool(info.unchecked), "angle_bound": info.angle_bound, "diff_bound": info.diff_bound,
-            "angle_limit": info.angle_limit, "diff_limit": info.diff_limit}
+    return {"unchecked": bool(info.unchecked), "carried": bool(info.carried), "angle_bound": info.angle_bound,
+            "diff_bound": info.diff_bound, "angle_limit": info.angle_limit, "diff_limit": info.diff_limit}
 
 
 def ftle_flowmap_bytes(dim: int, n_nodes: int, precision) -> int:

@@ -147,6 +147,20 @@ def test_abc_carried_turn_is_third_order_and_within_the_difference_bound(F, A, B
     assert worst[0] < 0.05 * b["diff_bound"], (worst, b)
 
 
+def test_carry_decision(F):
+    """The ABC step carries stage one's pairs only while the step's angle bound stays within
+    0.032 rad (its shorter stage-four turn then drops less than 4.4e-8): the 3D workload's step
+    carries, a longer unchecked step does not, and the double gyre never does."""
+    d = F.ftle_rotation_bounds(I.FlowSpec.abc(), 0.01)
+    assert d["unchecked"] and d["carried"] and d["angle_bound"] < 0.032
+    longer = F.ftle_rotation_bounds(I.FlowSpec.abc(), 0.011)
+    assert longer["unchecked"] and not longer["carried"] and longer["angle_bound"] > 0.032
+    edge = F.ftle_rotation_bounds(I.FlowSpec.abc(2.0, 0.5, 1.0), 0.01)  # angle bound 0.03
+    assert edge["unchecked"] and edge["carried"]
+    assert not F.ftle_rotation_bounds(I.FlowSpec.abc(), 0.02)["carried"]  # checked step
+    assert not F.ftle_rotation_bounds(I.FlowSpec.double_gyre(), 0.01)["carried"]
+
+
 def test_unchecked_decision_and_validation(F):
     dg = F.ftle_rotation_bounds(I.FlowSpec.double_gyre(), 0.01)
     assert dg["unchecked"] and dg["angle_bound"] < dg["angle_limit"] and dg["diff_bound"] < dg["diff_limit"]
