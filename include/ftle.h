@@ -131,7 +131,7 @@ typedef struct ftle_flow {
 typedef struct ftle_counters {
   unsigned long long n_flagged;    /* nodes whose gradient/eigenvalues went to the FP64 path */
   unsigned long long n_degenerate; /* nodes with a rank-deficient neighbourhood: FTLE = NaN */
-  unsigned long long n_readvected; /* nodes re-advected in FP64 by ftle_refine */
+  unsigned long long n_readvected; /* nodes re-advected in float-float by ftle_refine */
   unsigned long long reserved[4];
   unsigned long long n_wait_timeouts; /* bounded waits of a kernel that ran out (a stalled copy);
                                          the kernel's blocks stop, their outputs are incomplete */
@@ -260,7 +260,8 @@ int ftle_gradient_eig(const ftle_mesh* mesh, const void* flowmap, int32_t precis
 /* FP32C only (no-op for other precisions): re-advects in float-float arithmetic (~48 bits, on
  * the FP32 pipes) the nodes listed by the last ftle_gradient_eig on this workspace together
  * with their neighbours, writes their flowmap back as (hi, lo) pairs, and recomputes the listed
- * nodes' FTLE in FP64.  Must follow
+ * nodes' FTLE in FP64.  For the 2D double gyre and the 3D ABC flow a node's horizon is split into
+ * runs integrated side by side and joined through each run's tangent.  Must follow
  * ftle_gradient_eig on the same stream, mesh, flowmap and workspace. */
 int ftle_refine(const ftle_mesh* mesh, const ftle_flow* flow, double t0, double T, double dt,
                 int32_t precision, void* flowmap, void* ftle_out, double* lambda_out,
